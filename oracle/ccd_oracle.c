@@ -1,0 +1,355 @@
+/*
+ * ccd_oracle.c -- plain, slow, single-query CPU oracle for the inclusion-based
+ * CCD root finder of Wang et al., "A Large Scale Benchmark and an
+ * Inclusion-Based Algorithm for Continuous Collision Detection" (Sec. 4,
+ * Algorithm 2; minimum separation: Sec. 5).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  The GPU library never
+ * links, includes or calls it, and it shares no code with the GPU library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fopenmp -shared -fPIC
+ * (no FMA contraction: every + - * below is one IEEE double operation,
+ * rounded to nearest, in the order written).
+ *
+ * Query layout: 24 doubles, index = time*12 + point*3 + coord, i.e. the four
+ * points at t0 followed by the four points at t1 (Appendix A ordering).
+ * Vertex-face (VF): points (p, v1, v2, v3).  Edge-edge (EE): (p1, p2, p3, p4).
+ *
+ * Readings of the paper taken here (each listed in the design notes):
+ *  - Box order: Q is ordered by (level, left end of I_t); ties keep insertion
+ *    order (a stable sort), children inserted left then right.
+ *  - A colliding box that meets the termination test but is not the first
+ *    colliding box of its level is split like a too-large box (the literal
+ *    Algorithm 2 drops it; flag ORACLE_LITERAL_DROP restores that).
+ *  - The returned tolerance is the co-domain width w(B) of the box checked
+ *    when the algorithm returns; no collision returns (inf, 0).
+ *  - w(B) and the box-inside test use the un-enlarged width / enlarged box.
+ *  - A split whose dimension already has width 2^-53 is not made: the query
+ *    returns as at the check limit (keeps every endpoint an exact double).
+ *  - F is evaluated with the fixed expression in corner_F below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_LITERAL_DROP 1
+
+/* Sec. 3, "Multivariate CCD Formulation": linear trajectory
+ * p(t) = (1-t) p^0 + t p^1, evaluated as p^0 + (p^1 - p^0) t. */
+static double traj(const double *q, int point, int c, double t)
+{
+    double x0 = q[point * 3 + c];
+    double x1 = q[12 + point * 3 + c];
+    double d = x1 - x0;
+    return x0 + d * t;
+}
+
+/* Eq. (F-vf) and Eq. (F-ee), written in a fixed operation order:
+ *   VF: q = p - v1, e1 = v2 - v1, e2 = v3 - v1;  F = (q - u e1) - v e2
+ *       (equals p - ((1-u-v) v1 + u v2 + v v3)).
+ *   EE: d1 = p2 - p1, d2 = p4 - p3;  F = (p1 + u d1) - (p3 + v d2)
+ *       (equals ((1-u) p1 + u p2) - ((1-v) p3 + v p4)).
+ * All positions are taken at time t first. */
+void oracle_corner(int kind, const double *q, double t, double u, double v,
+                   double F[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        double a = traj(q, 0, c, t);
+        double b = traj(q, 1, c, t);
+        double e = traj(q, 2, c, t);
+        double f = traj(q, 3, c, t);
+        if (kind == 0) {
+            double qq = a - b;   /* p - v1  */
+            double e1 = e - b;   /* v2 - v1 */
+            double e2 = f - b;   /* v3 - v1 */
+            F[c] = (qq - u * e1) - v * e2;
+        } else {
+            double d1 = b - a;   /* p2 - p1 */
+            double d2 = f - e;   /* p4 - p3 */
+            F[c] = (a + u * d1) - (e + v * d2);
+        }
+    }
+}
+
+/* Eq. (box): B_F(I) is the axis-aligned box of F at the 8 corners of I. */
+void oracle_box(int kind, const double *q, const double I[6], double m[3],
+                double M[3])
+{
+    int first = 1;
+    for (int it = 0; it < 2; ++it)
+        for (int iu = 0; iu < 2; ++iu)
+            for (int iv = 0; iv < 2; ++iv) {
+                double F[3];
+                oracle_corner(kind, q, I[it], I[2 + iu], I[4 + iv], F);
+                for (int c = 0; c < 3; ++c) {
+                    if (first || F[c] < m[c]) m[c] = F[c];
+                    if (first || F[c] > M[c]) M[c] = F[c];
+                }
+                first = 0;
+            }
+}
+
+/* Eq. (kappas): kappa_t = 3 max_{u,v in {0,1}} ||F(0,u,v) - F(1,u,v)||_inf,
+ * and likewise along u and v, over the corners of the domain [0,1]^3. */
+void oracle_kappa(int kind, const double *q, double kappa[3])
+{
+    double F[2][2][2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c)
+                oracle_corner(kind, q, (double)a, (double)b, (double)c, F[a][b][c]);
+    double kt = 0.0, ku = 0.0, kv = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int c = 0; c < 3; ++c) {
+                double dt = fabs(F[0][i][j][c] - F[1][i][j][c]);
+                double du = fabs(F[i][0][j][c] - F[i][1][j][c]);
+                double dv = fabs(F[i][j][0][c] - F[i][j][1][c]);
+                if (dt > kt) kt = dt;
+                if (du > ku) ku = du;
+                if (dv > kv) kv = dv;
+            }
+    kappa[0] = 3.0 * kt;
+    kappa[1] = 3.0 * ku;
+    kappa[2] = 3.0 * kv;
+}
+
+/* Eq. (ccd-error) and Eq. (msccd-error): eps^c = K gamma_c^3 with
+ * gamma_c = max(max_i |x_i^c|, 1).  The four constants are the paper's. */
+static const double K_VF = 6.661338147750939e-15;
+static const double K_EE = 6.217248937900877e-15;
+static const double K_VF_MS = 7.549516567451064e-15;
+static const double K_EE_MS = 7.105427357601002e-15;
+
+double oracle_filter_constant(int kind, int ms_nonzero)
+{
+    if (kind == 0) return ms_nonzero ? K_VF_MS : K_VF;
+    return ms_nonzero ? K_EE_MS : K_EE;
+}
+
+/* Sec. 6: the tolerances may be taken over a whole scene.  per_query != 0
+ * gives one eps triple per query (n x 3), else one triple over all points. */
+void oracle_err_from_bounds(int kind, const double *verts, long long n,
+                            int ms_nonzero, int per_query, double *err_out)
+{
+    double K = oracle_filter_constant(kind, ms_nonzero);
+    double g[3] = {1.0, 1.0, 1.0};
+    for (long long i = 0; i < n; ++i) {
+        const double *q = verts + 24 * i;
+        if (per_query) g[0] = g[1] = g[2] = 1.0;
+        for (int k = 0; k < 8; ++k)
+            for (int c = 0; c < 3; ++c) {
+                double a = fabs(q[k * 3 + c]);
+                if (a > g[c]) g[c] = a;
+            }
+        if (per_query)
+            for (int c = 0; c < 3; ++c)
+                err_out[3 * i + c] = K * ((g[c] * g[c]) * g[c]);
+    }
+    if (!per_query)
+        for (int c = 0; c < 3; ++c)
+            err_out[c] = K * ((g[c] * g[c]) * g[c]);
+}
+
+/* ---- the priority queue Q of Algorithm 2 -------------------------------- */
+
+typedef struct {
+    int level;
+    unsigned long long seq; /* insertion counter: stable order among ties */
+    double I[6];            /* tL, tR, uL, uR, vL, vR */
+} entry;
+
+typedef struct {
+    entry *a;
+    long long size, cap;
+    unsigned long long next_seq;
+} heap;
+
+/* order(): level first, then the left end of I_t, then insertion order. */
+static int before(const entry *x, const entry *y)
+{
+    if (x->level != y->level) return x->level < y->level;
+    if (x->I[0] != y->I[0]) return x->I[0] < y->I[0];
+    return x->seq < y->seq;
+}
+
+static int heap_push(heap *h, int level, const double I[6])
+{
+    if (h->size == h->cap) {
+        long long nc = h->cap ? 2 * h->cap : 64;
+        entry *na = (entry *)realloc(h->a, (size_t)nc * sizeof(entry));
+        if (!na) return -1;
+        h->a = na;
+        h->cap = nc;
+    }
+    entry e;
+    e.level = level;
+    e.seq = h->next_seq++;
+    memcpy(e.I, I, sizeof(e.I));
+    long long i = h->size++;
+    while (i > 0) {
+        long long p = (i - 1) / 2;
+        if (!before(&e, &h->a[p])) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i] = e;
+    return 0;
+}
+
+static entry heap_pop(heap *h)
+{
+    entry top = h->a[0];
+    entry last = h->a[--h->size];
+    long long i = 0;
+    for (;;) {
+        long long l = 2 * i + 1, r = l + 1, s = i;
+        const entry *best = &last;
+        if (l < h->size && before(&h->a[l], best)) { s = l; best = &h->a[l]; }
+        if (r < h->size && before(&h->a[r], best)) { s = r; best = &h->a[r]; }
+        if (s == i) break;
+        h->a[i] = h->a[s];
+        i = s;
+    }
+    if (h->size > 0) h->a[i] = last;
+    return top;
+}
+
+/* ---- Algorithm 2 (with the minimum-separation change of Sec. 5.1) -------- */
+
+/* Returns 1 (collision) or 0; -1 if memory for Q could not be obtained.
+ * toi: left end of the recorded first colliding t-interval, or +inf.
+ * out_tol: w(B) of the box checked at return, or 0.  checks: n. */
+int oracle_ccd(int kind, const double *q, const double err[3], double ms,
+               double delta, long long max_itr, int flags, double *toi,
+               double *out_tol, long long *checks)
+{
+    double kappa[3];
+    oracle_kappa(kind, q, kappa);
+
+    heap Q = {0};
+    const double root[6] = {0.0, 1.0, 0.0, 1.0, 0.0, 1.0};
+    if (heap_push(&Q, 0, root)) return -1;
+
+    long long n = 0;
+    int lp = -1;
+    double If_left = 0.0;
+    int result = 0;
+    double r_toi = INFINITY, r_tol = 0.0;
+
+    while (Q.size > 0) {
+        entry e = heap_pop(&Q);
+        const double *I = e.I;
+        double m[3], M[3];
+        oracle_box(kind, q, I, m, M);
+        n += 1;
+
+        /* B intersects C_eps: every axis interval, moved out by ms, meets
+         * [-eps, eps]. */
+        int hit = 1;
+        for (int c = 0; c < 3; ++c)
+            if (!((m[c] - ms) <= err[c] && (M[c] + ms) >= -err[c])) hit = 0;
+        if (!hit) continue;
+
+        int first = (e.level != lp);
+        if (first) If_left = I[0];
+
+        double wB = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double w = M[c] - m[c];
+            if (w > wB) wB = w;
+        }
+
+        if (n >= max_itr) {
+            result = 1; r_toi = If_left; r_tol = wB;
+            break;
+        }
+
+        int inside = 1;
+        for (int c = 0; c < 3; ++c)
+            if (!((m[c] - ms) >= -err[c] && (M[c] + ms) <= err[c])) inside = 0;
+
+        if (wB < delta || inside) {
+            if (first) {
+                result = 1; r_toi = If_left; r_tol = wB;
+                break;
+            }
+            if (flags & ORACLE_LITERAL_DROP) {
+                lp = e.level;
+                continue;
+            }
+        }
+
+        /* split(): c_d = w(I_d) kappa_d, widest estimated co-domain extent,
+         * ties resolved t, then u, then v. */
+        double ct = (I[1] - I[0]) * kappa[0];
+        double cu = (I[3] - I[2]) * kappa[1];
+        double cv = (I[5] - I[4]) * kappa[2];
+        double cmax = ct;
+        if (cu > cmax) cmax = cu;
+        if (cv > cmax) cmax = cv;
+        int dim = (ct == cmax) ? 0 : (cu == cmax) ? 1 : 2;
+
+        double L = I[2 * dim], R = I[2 * dim + 1];
+        if (R - L <= 0x1p-53) { /* depth guard */
+            result = 1; r_toi = If_left; r_tol = wB;
+            break;
+        }
+        double mid = (L + R) / 2.0;
+        double I1[6], I2[6];
+        memcpy(I1, I, sizeof(I1));
+        memcpy(I2, I, sizeof(I2));
+        I1[2 * dim + 1] = mid;
+        I2[2 * dim] = mid;
+
+        /* VF: keep a child only if it meets the prism u, v >= 0, u + v <= 1,
+         * i.e. uL + vL <= 1 (tested as uL <= 1 - vL, exact for these
+         * dyadic endpoints). */
+        int keep1 = 1, keep2 = 1;
+        if (kind == 0) {
+            keep1 = I1[2] <= 1.0 - I1[4];
+            keep2 = I2[2] <= 1.0 - I2[4];
+        }
+        if (keep1 && heap_push(&Q, e.level + 1, I1)) { result = -1; break; }
+        if (keep2 && heap_push(&Q, e.level + 1, I2)) { result = -1; break; }
+        lp = e.level;
+    }
+    free(Q.a);
+    if (toi) *toi = r_toi;
+    if (out_tol) *out_tol = r_tol;
+    if (checks) *checks = n;
+    return result;
+}
+
+/* Batch driver: one oracle_ccd per query (queries are independent; OpenMP
+ * only spreads whole queries over host threads). verts: n x 24 doubles;
+ * err: 3 doubles (err_stride 0) or n x 3 (err_stride 3).  Returns the number
+ * of queries whose Q could not be allocated (their result is left as a
+ * conservative collision at t = 0). */
+long long oracle_ccd_batch(int kind, const double *verts, long long n,
+                           const double *err, int err_stride, double ms,
+                           double delta, long long max_itr, int flags,
+                           unsigned char *collides, double *toi,
+                           double *out_tol, long long *checks, int nthreads)
+{
+    long long failures = 0;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads) reduction(+ : failures)
+    for (long long i = 0; i < n; ++i) {
+        double t, w;
+        long long c;
+        int r = oracle_ccd(kind, verts + 24 * i, err + (long long)err_stride * i,
+                           ms, delta, max_itr, flags, &t, &w, &c);
+        if (r < 0) {
+            failures += 1;
+            r = 1; t = 0.0; w = INFINITY;
+        }
+        collides[i] = (unsigned char)r;
+        toi[i] = t;
+        out_tol[i] = w;
+        if (checks) checks[i] = c;
+    }
+    return failures;
+}

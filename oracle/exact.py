@@ -1,0 +1,169 @@
+"""Exact-rational companion of the oracle (TEST INFRASTRUCTURE ONLY).
+
+Everything here uses ``fractions.Fraction`` and the paper's own algebraic
+forms, independently of the floating-point operation order in
+``ccd_oracle.c``:
+
+* ``F`` -- Eq. (F-vf) / (F-ee) as printed: barycentric / edge-parameter
+  combinations of the linearly interpolated points.
+* ``solve`` -- Algorithm 2 run in exact arithmetic with a Python list that is
+  stably re-sorted by (level, left end of I_t) after every insertion, i.e. the
+  literal "Q <- Q u {I1, I2}; sort(Q, order)" of the paper.  With eps = 0 and
+  exact arithmetic, an emptied queue certifies that F has no root in the
+  domain (B_F is an inclusion function, Proposition 1).
+* ``coplanarity_cubic`` -- f(t) = <n(t), q(t)> of Eq. (univariate).
+"""
+from __future__ import annotations
+
+from fractions import Fraction as Fr
+from typing import Sequence
+
+VF, EE = 0, 1
+
+
+def to_fr(query: Sequence[float]) -> list[Fr]:
+    return [Fr(float(x)) for x in query]
+
+
+def point(q: Sequence[Fr], i: int, t: Fr) -> list[Fr]:
+    """p_i(t) = (1 - t) p_i^0 + t p_i^1 (Sec. 3)."""
+    return [(1 - t) * q[i * 3 + c] + t * q[12 + i * 3 + c] for c in range(3)]
+
+
+def F(kind: int, q: Sequence[Fr], t: Fr, u: Fr, v: Fr) -> list[Fr]:
+    """Eq. (F-vf) for kind VF, Eq. (F-ee) for kind EE, in exact arithmetic."""
+    a, b, c, d = (point(q, i, t) for i in range(4))
+    if kind == VF:
+        return [a[k] - ((1 - u - v) * b[k] + u * c[k] + v * d[k]) for k in range(3)]
+    return [((1 - u) * a[k] + u * b[k]) - ((1 - v) * c[k] + v * d[k]) for k in range(3)]
+
+
+def box(kind: int, q, I) -> tuple[list[Fr], list[Fr]]:
+    """Exact B_F(I): per-axis min / max over the 8 corners (Eq. box)."""
+    vals = [F(kind, q, t, u, v) for t in I[0:2] for u in I[2:4] for v in I[4:6]]
+    m = [min(x[k] for x in vals) for k in range(3)]
+    M = [max(x[k] for x in vals) for k in range(3)]
+    return m, M
+
+
+def kappa(kind: int, q) -> list[Fr]:
+    """Eq. (kappas) in exact arithmetic."""
+    one, zero = Fr(1), Fr(0)
+    out = []
+    for dim in range(3):
+        best = Fr(0)
+        for i in (zero, one):
+            for j in (zero, one):
+                lo = [zero, zero, zero]
+                hi = [one, one, one]
+                others = [k for k in range(3) if k != dim]
+                lo[others[0]] = hi[others[0]] = i
+                lo[others[1]] = hi[others[1]] = j
+                A = F(kind, q, *lo)
+                B = F(kind, q, *hi)
+                best = max(best, max(abs(A[k] - B[k]) for k in range(3)))
+        out.append(3 * best)
+    return out
+
+
+def solve(kind: int, query, delta, max_itr: int, ms=0, err=(0, 0, 0),
+          literal_drop: bool = False):
+    """Algorithm 2 in exact arithmetic.  Returns (collides, toi, w(B), checks).
+
+    ``err`` is the per-axis half-width of C_eps (0 for a pure exact run);
+    the same readings as the C oracle apply (stable order, split-anyway for a
+    non-first terminating box unless ``literal_drop``, out_tol = w(B), depth
+    guard at width 2^-53).
+    """
+    q = query if isinstance(query[0], Fr) else to_fr(query)
+    delta = Fr(delta)
+    ms = Fr(ms)
+    err = [Fr(e) for e in err]
+    kap = kappa(kind, q)
+    Q = [(0, [Fr(0), Fr(1), Fr(0), Fr(1), Fr(0), Fr(1)])]
+    n = 0
+    lp = -1
+    If_left = None
+    while Q:
+        level, I = Q.pop(0)
+        m, M = box(kind, q, I)
+        n += 1
+        hit = all(m[c] - ms <= err[c] and M[c] + ms >= -err[c] for c in range(3))
+        if not hit:
+            continue
+        first = level != lp
+        if first:
+            If_left = I[0]
+        wB = max(M[c] - m[c] for c in range(3))
+        if n >= max_itr:
+            return True, If_left, wB, n
+        inside = all(m[c] - ms >= -err[c] and M[c] + ms <= err[c] for c in range(3))
+        if wB < delta or inside:
+            if first:
+                return True, If_left, wB, n
+            if literal_drop:
+                lp = level
+                continue
+        c = [(I[2 * d + 1] - I[2 * d]) * kap[d] for d in range(3)]
+        cm = max(c)
+        dim = 0 if c[0] == cm else (1 if c[1] == cm else 2)
+        L, R = I[2 * dim], I[2 * dim + 1]
+        if R - L <= Fr(1, 2**53):
+            return True, If_left, wB, n
+        mid = (L + R) / 2
+        I1, I2 = list(I), list(I)
+        I1[2 * dim + 1] = mid
+        I2[2 * dim] = mid
+        for child in (I1, I2):
+            if kind == VF and child[2] + child[4] > 1:
+                continue
+            Q.append((level + 1, child))
+        Q.sort(key=lambda e: (e[0], e[1][0]))  # stable: ties keep insertion order
+        lp = level
+    return False, None, Fr(0), n
+
+
+def coplanarity_cubic(kind: int, query) -> list[Fr]:
+    """Coefficients [c0, c1, c2, c3] of f(t) = <n(t), q(t)> (Eq. univariate):
+    VF: n = (v2 - v1) x (v3 - v1), q = p - v1;
+    EE: n = (p2 - p1) x (p4 - p3), q = p3 - p1."""
+    q = query if isinstance(query[0], Fr) else to_fr(query)
+
+    # Each point is affine in t: P(t) = P0 + t (P1 - P0); work with polynomials.
+    def poly_point(i):
+        return [[q[i * 3 + c], q[12 + i * 3 + c] - q[i * 3 + c]] for c in range(3)]
+
+    def sub(A, B):
+        return [[A[c][0] - B[c][0], A[c][1] - B[c][1]] for c in range(3)]
+
+    def pmul(a, b):
+        out = [Fr(0)] * (len(a) + len(b) - 1)
+        for i, x in enumerate(a):
+            for j, y in enumerate(b):
+                out[i + j] += x * y
+        return out
+
+    def padd(a, b):
+        n = max(len(a), len(b))
+        return [(a[i] if i < len(a) else 0) + (b[i] if i < len(b) else 0) for i in range(n)]
+
+    def psub(a, b):
+        return padd(a, [-x for x in b])
+
+    def cross(A, B):
+        return [psub(pmul(A[1], B[2]), pmul(A[2], B[1])),
+                psub(pmul(A[2], B[0]), pmul(A[0], B[2])),
+                psub(pmul(A[0], B[1]), pmul(A[1], B[0]))]
+
+    P = [poly_point(i) for i in range(4)]
+    if kind == VF:
+        n = cross(sub(P[2], P[1]), sub(P[3], P[1]))
+        qq = sub(P[0], P[1])
+    else:
+        n = cross(sub(P[1], P[0]), sub(P[3], P[2]))
+        qq = sub(P[2], P[0])
+    f = [Fr(0)]
+    for c in range(3):
+        f = padd(f, pmul(n[c], qq[c]))
+    f = f + [Fr(0)] * (4 - len(f))
+    return f[:4]
