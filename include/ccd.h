@@ -1,0 +1,147 @@
+/*
+ * ccd.h -- C ABI of the GB300 (sm_103a) batched inclusion-based continuous
+ * collision detection root finder.
+ *
+ * Method: Wang, Ferguson, Schneider, Jiang, Attene, Panozzo, "A Large Scale
+ * Benchmark and an Inclusion-Based Algorithm for Continuous Collision
+ * Detection", ACM TOG 40(5), 2021.  Every query solves Algorithm 2 (Sec. 4):
+ * breadth-first bisection of the parameter box [0,1]^3 of F(t,u,v)
+ * (Eq. F-vf, Eq. F-ee) with the box inclusion function B_F (Eq. box), the
+ * conservative floating-point filter eps (Eq. ccd-error), the kappa-weighted
+ * widest-dimension split (Eq. kappas), tolerance delta and the check limit
+ * m_I; with minimum separation d > 0 the box is enlarged by d (Sec. 5.1).
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller; the library
+ *    never allocates, frees or retains them.  Calls are asynchronous on
+ *    `stream` (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *  - verts: structure of arrays, 24 planes of n doubles (plane stride n).
+ *    Plane k holds coordinate k%3 of point (k/3)%4 at time k/12 (t0 for
+ *    k < 12, t1 for k >= 12).  Vertex-face (VF) points are (p, v1, v2, v3);
+ *    edge-edge (EE) points are (p1, p2, p3, p4) (Appendix A ordering).
+ *  - Inputs must be finite.  n must be below 2^31.
+ *  - Floating point is IEEE binary64, round to nearest, never contracted.
+ *
+ * Status codes are returned by value; errors found on the device are
+ * recorded in the workspace and read with ccd_workspace_status().
+ */
+#ifndef CCD_GB300_H
+#define CCD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCD_OK = 0,
+    CCD_ERR_ARG = -1,       /* invalid argument (checked on the host)          */
+    CCD_ERR_WORKSPACE = -2, /* workspace too small for even one deep slot      */
+    CCD_ERR_TIMEOUT = -3,   /* a bounded device wait gave up                   */
+    CCD_ERR_CUDA = -4,      /* a CUDA launch or copy failed                    */
+    CCD_ERR_CAPACITY = -5   /* device: a frontier exceeded its slot; the query
+                               was answered conservatively (see ccd_vf_batch)  */
+} ccd_status;
+
+#define CCD_KIND_VF 0
+#define CCD_KIND_EE 1
+
+/*
+ * Bytes of device workspace that ccd_vf_batch / ccd_ee_batch need for n
+ * queries at check limit max_itr with the default number of deep slots (one
+ * per SM of the current device).  A smaller workspace is accepted as long as
+ * it holds at least one deep slot; fewer slots only reduce parallelism on
+ * queries with very large subdivision frontiers.  Returns 0 on bad arguments.
+ */
+size_t ccd_workspace_bytes(int64_t n, int64_t max_itr);
+
+/*
+ * Batched vertex-face CCD (Algorithm 2 on F_vf, Eq. F-vf; prism-culled
+ * splits, Sec. 4.2).
+ *
+ *  verts    [24][n] f64  query points (layout above).
+ *  n        number of queries, 0 <= n < 2^31 (n = 0 is a no-op).
+ *  err      eps per axis (Eq. ccd-error; with ms > 0 Eq. msccd-error):
+ *           3 doubles shared by all queries when err_stride == 0, or
+ *           [n][3] doubles when err_stride == 3.  ccd_err_from_bounds
+ *           computes them.
+ *  ms       minimum separation d >= 0 (L-infinity, Sec. 5.1); 0 = plain CCD.
+ *  delta    tolerance delta > 0 on the co-domain width w(B).
+ *  max_itr  check limit m_I > 0.
+ *  collides [n] u8   1 if a (conservative) collision was found, else 0.
+ *  toi      [n] f64  conservative time of impact: left end of the first
+ *           colliding t-interval of the last level reached; +inf when
+ *           collides == 0.
+ *  out_tol  [n] f64  co-domain width w(B) of the box checked when the query
+ *           returned (the reached tolerance); 0 when collides == 0.
+ *  checks   [n] i64  number of box checks n of Algorithm 2; may be NULL.
+ *  workspace, ws_bytes  device scratch (see ccd_workspace_bytes); it must
+ *           not be used by another call that may overlap on the device.
+ *
+ * Results are deterministic and independent of the launch configuration.
+ * A query whose frontier does not fit its deep slot (only possible when the
+ * workspace holds fewer than 2*max_itr boxes per slot) returns as at the
+ * check limit -- collides = 1, toi = left end of the current level's first
+ * colliding t-interval -- and the workspace status becomes CCD_ERR_CAPACITY.
+ * Returns CCD_ERR_ARG for n < 0, n >= 2^31, delta <= 0 or NaN, max_itr <= 0,
+ * ms < 0 or NaN, err_stride not in {0, 3}, or a NULL array with n > 0;
+ * CCD_ERR_WORKSPACE if the workspace is NULL or too small; CCD_ERR_CUDA if a
+ * launch fails.
+ */
+ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err,
+                        int err_stride, double ms, double delta, int64_t max_itr,
+                        uint8_t *collides, double *toi, double *out_tol,
+                        int64_t *checks, void *workspace, size_t ws_bytes,
+                        void *stream);
+
+/*
+ * Batched edge-edge CCD (Algorithm 2 on F_ee, Eq. F-ee; no culling since
+ * the domain is the whole cube).  Arguments, outputs and errors exactly as
+ * for ccd_vf_batch.
+ */
+ccd_status ccd_ee_batch(const double *verts, int64_t n, const double *err,
+                        int err_stride, double ms, double delta, int64_t max_itr,
+                        uint8_t *collides, double *toi, double *out_tol,
+                        int64_t *checks, void *workspace, size_t ws_bytes,
+                        void *stream);
+
+/*
+ * Floating-point filter eps (Eq. ccd-error, Eq. msccd-error):
+ * eps_c = K * gamma_c^3 with gamma_c = max(max_i |x_i^c|, 1), computed as
+ * K * ((gamma * gamma) * gamma), K = 30, 28, 34, 32 * 2^-52 for VF, EE,
+ * VF with ms, EE with ms.  per_query == 0 takes the maximum over all points
+ * of all n queries (scene-wide tolerance, Sec. 6) and writes 3 doubles;
+ * per_query != 0 writes [n][3].  err_out is a device pointer.  The ms
+ * constants assume d < gamma (Sec. 5.1).
+ */
+ccd_status ccd_err_from_bounds(int kind, const double *verts, int64_t n,
+                               int ms_nonzero, int per_query, double *err_out,
+                               void *stream);
+
+/*
+ * Device status recorded in the workspace by the last call that used it:
+ * CCD_OK or CCD_ERR_CAPACITY; *fallbacks (may be NULL) receives how many
+ * queries were answered by the capacity fallback.  Synchronizes `stream`.
+ */
+ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
+                                int32_t *fallbacks, void *stream);
+
+/* Static description of a status code. */
+const char *ccd_status_str(int status);
+
+/*
+ * FP64 pipe throughput probe used for the roofline denominator: runs
+ * `blocks` x 256 threads of independent fma.rn.f64 chains for `iters`
+ * iterations and writes the elapsed device milliseconds to *ms_out.
+ * Synchronizes `stream`.  The number of FP64 operations issued is
+ * blocks * 256 * iters * 8.
+ */
+ccd_status ccd_fp64_peak_probe(int blocks, int iters, float *ms_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCD_GB300_H */

@@ -1,0 +1,170 @@
+"""Thin Python binding of the C ABI in ``include/ccd.h`` (argument marshalling only).
+
+Every step of the path runs in the CUDA library ``_lib/libccd_gb300.so``;
+this module converts torch tensors to device pointers, allocates the caller-
+side workspace with torch, and raises if the library or a GPU is missing.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+VF, EE = 0, 1
+STATUS = {0: "CCD_OK", -1: "CCD_ERR_ARG", -2: "CCD_ERR_WORKSPACE", -3: "CCD_ERR_TIMEOUT",
+          -4: "CCD_ERR_CUDA", -5: "CCD_ERR_CAPACITY"}
+
+_LIB = None
+
+
+class CCDError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def lib():
+    """Load the CUDA library (fails loudly when it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, dp = ctypes.c_void_p, ctypes.c_void_p
+        i64, sz = ctypes.c_int64, ctypes.c_size_t
+        L.ccd_workspace_bytes.argtypes = [i64, i64]
+        L.ccd_workspace_bytes.restype = sz
+        for name in ("ccd_vf_batch", "ccd_ee_batch"):
+            f = getattr(L, name)
+            f.argtypes = [dp, i64, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, i64,
+                          vp, dp, dp, vp, vp, sz, vp]
+            f.restype = ctypes.c_int
+        L.ccd_err_from_bounds.argtypes = [ctypes.c_int, dp, i64, ctypes.c_int, ctypes.c_int, dp, vp]
+        L.ccd_err_from_bounds.restype = ctypes.c_int
+        L.ccd_workspace_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), vp]
+        L.ccd_workspace_status.restype = ctypes.c_int
+        L.ccd_status_str.argtypes = [ctypes.c_int]
+        L.ccd_status_str.restype = ctypes.c_char_p
+        L.ccd_fp64_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_float), vp]
+        L.ccd_fp64_peak_probe.restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise CCDError(code, what)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+
+
+def workspace_bytes(n: int, max_itr: int) -> int:
+    return int(lib().ccd_workspace_bytes(int(n), int(max_itr)))
+
+
+def workspace(n: int, max_itr: int, device=None) -> torch.Tensor:
+    """Caller-owned device workspace for ``n`` queries at check limit ``max_itr``."""
+    nbytes = workspace_bytes(n, max_itr)
+    if nbytes == 0:
+        raise CCDError(-1, "ccd_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class Result:
+    collides: torch.Tensor   # (n,) uint8
+    toi: torch.Tensor        # (n,) float64
+    out_tol: torch.Tensor    # (n,) float64
+    checks: torch.Tensor     # (n,) int64 or None
+
+
+def batch(kind: int, verts: torch.Tensor, err: torch.Tensor, ms: float = 0.0,
+          delta: float = 1e-6, max_itr: int = 10**6, ws: torch.Tensor | None = None,
+          out: Result | None = None, with_checks: bool = True, stream=None) -> Result:
+    """ccd_vf_batch / ccd_ee_batch.  ``verts``: (24, n) float64 CUDA tensor
+    (structure of arrays); ``err``: (3,) or (n, 3) float64 CUDA tensor."""
+    _require_cuda(verts, "verts", torch.float64)
+    if verts.dim() != 2 or verts.shape[0] != 24:
+        raise ValueError("verts must have shape (24, n)")
+    n = verts.shape[1]
+    _require_cuda(err, "err", torch.float64)
+    stride = 0 if err.numel() == 3 else 3
+    if stride == 3 and err.numel() != 3 * n:
+        raise ValueError("err must have 3 or 3*n elements")
+    dev = verts.device
+    if out is None:
+        out = Result(torch.empty(n, dtype=torch.uint8, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.int64, device=dev) if with_checks else None)
+    if ws is None:
+        ws = workspace(n, max_itr, dev)
+    fn = lib().ccd_vf_batch if kind == VF else lib().ccd_ee_batch
+    code = fn(_ptr(verts), n, _ptr(err), stride, float(ms), float(delta), int(max_itr),
+              _ptr(out.collides), _ptr(out.toi), _ptr(out.out_tol), _ptr(out.checks),
+              _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "ccd_vf_batch" if kind == VF else "ccd_ee_batch")
+    return out
+
+
+def vf_batch(verts, err, **kw) -> Result:
+    return batch(VF, verts, err, **kw)
+
+
+def ee_batch(verts, err, **kw) -> Result:
+    return batch(EE, verts, err, **kw)
+
+
+def err_from_bounds(kind: int, verts: torch.Tensor, ms_nonzero: bool = False,
+                    per_query: bool = False, stream=None) -> torch.Tensor:
+    _require_cuda(verts, "verts", torch.float64)
+    n = verts.shape[1]
+    out = torch.empty((n, 3) if per_query else (3,), dtype=torch.float64, device=verts.device)
+    _check(lib().ccd_err_from_bounds(kind, _ptr(verts), n, int(bool(ms_nonzero)),
+                                     int(bool(per_query)), _ptr(out), _stream(stream)),
+           "ccd_err_from_bounds")
+    return out
+
+
+def workspace_status(ws: torch.Tensor, stream=None):
+    st, fb = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ccd_workspace_status(_ptr(ws), ctypes.byref(st), ctypes.byref(fb),
+                                      _stream(stream)), "ccd_workspace_status")
+    return st.value, fb.value
+
+
+def fp64_peak_probe(blocks: int, iters: int, stream=None):
+    """Returns (ms, fp64 ops issued) of the FMA throughput probe."""
+    ms = ctypes.c_float()
+    _check(lib().ccd_fp64_peak_probe(int(blocks), int(iters), ctypes.byref(ms), _stream(stream)),
+           "ccd_fp64_peak_probe")
+    return ms.value, blocks * 256 * iters * 8
+
+
+def to_soa(verts_aos, device="cuda") -> torch.Tensor:
+    """(n, 24) host array -> (24, n) contiguous float64 device tensor."""
+    t = torch.as_tensor(verts_aos, dtype=torch.float64)
+    return t.t().contiguous().to(device)

@@ -1,0 +1,917 @@
+// ccd.cu -- sm_103a kernels and C ABI of the batched inclusion-based CCD root
+// finder (Wang et al. 2021, Sec. 4, Algorithm 2; minimum separation Sec. 5.1).
+//
+// Execution plan of one batch (all launches on the caller's stream, no host
+// synchronisation, no allocation):
+//   1. root_kernel     one thread per query: loads the 192-byte record,
+//                      checks the level-0 box [0,1]^3 (Eq. box, Eq.
+//                      ccd-error).  Queries rejected there, or terminating
+//                      there, are answered; the rest get kappa (Eq. kappas)
+//                      and join the survivor list.
+//   2. solve_kernel<32>   persistent; one warp per survivor query runs the
+//                      level-synchronous form of Algorithm 2 with its frontier
+//                      in a small private slot.  A query whose frontier
+//                      outgrows the slot moves to the overflow list.
+//   3. solve_kernel<512>  persistent; one 512-thread block per overflow query,
+//                      frontier slot sized for 2 m_I boxes (the most any
+//                      level can hold, see solve_query).
+//
+// Level-synchronous form of Algorithm 2.  Q is ordered by (level, left end
+// of I_t); ties keep insertion order, children inserted left then right.
+// All boxes of one level have the same widths, hence the same split
+// dimension.  A level is therefore an array in Q order: for u/v splits the
+// children of box j are adjacent (left, right); for t splits, each run of
+// boxes sharing I_t emits all left children, then all right children.  The
+// check counter of the box at array position i is n_before + i + 1, so the
+// first colliding box, the m_I cut-off and the termination test are decided
+// with block-wide min-reductions, exactly as the sequential loop would.
+//
+// Boxes are stored as integer numerators (a_t, a_u, a_v) of dyadic
+// endpoints a 2^-k, k <= 53 per dimension, converted to doubles exactly.
+// F is evaluated in the fixed order: positions x0 + (x1 - x0) t first; VF
+// F = (q - u e1) - v e2 with q = p - v1, e1 = v2 - v1, e2 = v3 - v1; EE
+// F = (p1 + u d1) - (p3 + v d2), d1 = p2 - p1, d2 = p4 - p3.  Every add and
+// multiply is an explicit round-to-nearest intrinsic (never contracted).
+
+#include "ccd.h"
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr int KMAX = 53;              // deepest dyadic level per dimension
+constexpr int ROOT_THREADS = 256;
+constexpr int SMALL_THREADS = 32;     // one warp per query
+constexpr int SMALL_BLOCKS_PER_SM = 16;
+constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
+constexpr int DEEP_THREADS = 512;
+constexpr int BIG = 0x7fffffff;
+constexpr long long BIGL = 0x7fffffffffffffffLL;
+
+struct Box {
+    unsigned long long a[3];          // numerators of (t_L, u_L, v_L)
+};
+
+struct Header {
+    int survivors;   // queries in the survivor list
+    int head_small;  // work counter of the small-frontier solver
+    int overflow;    // queries in the overflow list
+    int head_deep;   // work counter of the deep solver
+    int status;      // CCD_OK or CCD_ERR_CAPACITY
+    int fallbacks;   // queries answered by the capacity fallback
+    int pad[58];
+};
+static_assert(sizeof(Header) == 256, "header is one 256-byte line");
+
+struct Layout {
+    size_t off_surv, off_over, off_kappa, off_small, off_deep, total;
+    int nb_small, nb_deep;
+    long long cap_small, cap_deep;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- exact dyadic conversion and small helpers -----------------------------
+
+// a * 2^-k as a double, exact for 0 <= a <= 2^53 and 0 <= k <= 53 (integer
+// construction of the bit pattern; the FP64 pipe is not used).
+__device__ __forceinline__ double dyadic(unsigned long long a, int k)
+{
+    if (a == 0ull) return 0.0;
+    int lz = __clzll((long long)a);
+    int sh = lz - 11;                  // puts the leading one at bit 52
+    unsigned long long m = sh >= 0 ? (a << sh) : (a >> (-sh));
+    unsigned long long e = (unsigned long long)(1023 + (63 - lz) - k);
+    return __longlong_as_double((long long)((e << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ double pow2neg(int k)
+{
+    return __longlong_as_double((long long)((unsigned long long)(1023 - k) << 52));
+}
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+// ---- per-query data ---------------------------------------------------------
+
+struct Query {
+    double x0[12];   // points at t0
+    double dx[12];   // x1 - x0
+};
+
+__device__ __forceinline__ void load_query(const double *__restrict__ verts, long long n,
+                                           long long i, Query &Q)
+{
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double a = __ldg(verts + (size_t)k * n + i);
+        double b = __ldg(verts + (size_t)(12 + k) * n + i);
+        Q.x0[k] = a;
+        Q.dx[k] = dsub(b, a);
+    }
+}
+
+// B_F(I) of Eq. (box): per-axis min m and max M of F over the 8 corners.
+template <int KIND>
+__device__ __forceinline__ void box_eval(const Query &Q, double tl, double tr, double ul,
+                                         double ur, double vl, double vr, double (&m)[3],
+                                         double (&M)[3])
+{
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double t = it ? tr : tl;
+        double P[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) P[j] = dadd(Q.x0[j], dmul(Q.dx[j], t));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double f0, f1, f2, f3;
+            if (KIND == CCD_KIND_VF) {
+                double q = dsub(P[c], P[3 + c]);
+                double e1 = dsub(P[6 + c], P[3 + c]);
+                double e2 = dsub(P[9 + c], P[3 + c]);
+                double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
+                double bl = dmul(vl, e2), br = dmul(vr, e2);
+                f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+            } else {
+                double d1 = dsub(P[3 + c], P[c]);
+                double d2 = dsub(P[9 + c], P[6 + c]);
+                double al = dadd(P[c], dmul(ul, d1)), ar = dadd(P[c], dmul(ur, d1));
+                double bl = dadd(P[6 + c], dmul(vl, d2)), br = dadd(P[6 + c], dmul(vr, d2));
+                f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+            }
+            double lo = fmin(fmin(f0, f1), fmin(f2, f3));
+            double hi = fmax(fmax(f0, f1), fmax(f2, f3));
+            if (it == 0) { m[c] = lo; M[c] = hi; }
+            else { m[c] = fmin(m[c], lo); M[c] = fmax(M[c], hi); }
+        }
+    }
+}
+
+// The box test of Algorithm 2 with the Sec. 5.1 enlargement by ms.
+struct BoxTest {
+    bool hit;      // B (enlarged by ms) meets C_eps
+    bool term;     // w(B) < delta or enlarged B inside C_eps
+    double w;      // w(B), un-enlarged
+};
+
+__device__ __forceinline__ BoxTest box_test(const double (&m)[3], const double (&M)[3],
+                                            const double (&eps)[3], double ms, double delta)
+{
+    BoxTest r;
+    double lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = ms != 0.0 ? dsub(m[c], ms) : m[c];   // m - 0 == m
+        hi[c] = ms != 0.0 ? dadd(M[c], ms) : M[c];
+    }
+    r.hit = (lo[0] <= eps[0]) & (hi[0] >= -eps[0]) & (lo[1] <= eps[1]) & (hi[1] >= -eps[1]) &
+            (lo[2] <= eps[2]) & (hi[2] >= -eps[2]);
+    r.w = fmax(fmax(dsub(M[0], m[0]), dsub(M[1], m[1])), dsub(M[2], m[2]));
+    bool inside = (lo[0] >= -eps[0]) & (hi[0] <= eps[0]) & (lo[1] >= -eps[1]) &
+                  (hi[1] <= eps[1]) & (lo[2] >= -eps[2]) & (hi[2] <= eps[2]);
+    r.term = (r.w < delta) | inside;
+    return r;
+}
+
+// ---- block primitives (BS = 32: warp only; BS > 32: warp + shared) ---------
+
+template <int BS>
+__device__ __forceinline__ void bsync()
+{
+    if (BS == 32) __syncwarp(); else __syncthreads();
+}
+
+__device__ __forceinline__ int warp_min(int v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ long long warp_minl(long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ long long warp_maxl(long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int BS>
+struct Smem {
+    int ired[BS / 32 + 1];
+    long long lred[BS / 32 + 1];
+    unsigned long long first_at;
+    double first_w;
+    int first_term;
+    double cut_w;
+};
+
+template <int BS>
+__device__ __forceinline__ int block_min(int v, Smem<BS> &s)
+{
+    v = warp_min(v);
+    if (BS == 32) return v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s.ired[warp] = v;
+    __syncthreads();
+    int r = lane < BS / 32 ? s.ired[lane] : BIG;
+    r = warp_min(r);
+    __syncthreads();
+    return r;
+}
+
+template <int BS>
+__device__ __forceinline__ long long block_minl(long long v, Smem<BS> &s)
+{
+    v = warp_minl(v);
+    if (BS == 32) return v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s.lred[warp] = v;
+    __syncthreads();
+    long long r = lane < BS / 32 ? s.lred[lane] : BIGL;
+    r = warp_minl(r);
+    __syncthreads();
+    return r;
+}
+
+template <int BS>
+__device__ __forceinline__ long long block_maxl(long long v, Smem<BS> &s)
+{
+    v = warp_maxl(v);
+    if (BS == 32) return v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s.lred[warp] = v;
+    __syncthreads();
+    long long r = lane < BS / 32 ? s.lred[lane] : -1;
+    r = warp_maxl(r);
+    __syncthreads();
+    return r;
+}
+
+// exclusive prefix sum of v over the block (thread order); *total = sum
+template <int BS>
+__device__ __forceinline__ int block_excl_scan(int v, int *total, Smem<BS> &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (BS == 32) {
+        *total = __shfl_sync(0xffffffffu, inc, 31);
+        return inc - v;
+    }
+    if (lane == 31) s.ired[warp] = inc;
+    __syncthreads();
+    int ws = lane < BS / 32 ? s.ired[lane] : 0;
+    int wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+    }
+    int before = __shfl_sync(0xffffffffu, wi - ws, warp);
+    *total = __shfl_sync(0xffffffffu, wi, BS / 32 - 1);
+    __syncthreads();
+    return before + inc - v;
+}
+
+// inclusive max-scan over thread order (values >= -1)
+template <int BS>
+__device__ __forceinline__ long long block_incl_maxscan(long long v, Smem<BS> &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = max(inc, y);
+    }
+    if (BS == 32) return inc;
+    if (lane == 31) s.lred[warp] = inc;
+    __syncthreads();
+    long long prev = -1;
+    for (int w = 0; w < warp; ++w) prev = max(prev, s.lred[w]);
+    __syncthreads();
+    return max(prev, inc);
+}
+
+// inclusive min-scan over reversed thread order: min over threads >= me
+template <int BS>
+__device__ __forceinline__ long long block_suffix_min(long long v, Smem<BS> &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_down_sync(0xffffffffu, inc, o);
+        if (lane + o < 32) inc = min(inc, y);
+    }
+    if (BS == 32) return inc;
+    if (lane == 0) s.lred[warp] = inc;
+    __syncthreads();
+    long long nxt = BIGL;
+    for (int w = warp + 1; w < BS / 32; ++w) nxt = min(nxt, s.lred[w]);
+    __syncthreads();
+    return min(nxt, inc);
+}
+
+// ---- kernel parameters ------------------------------------------------------
+
+struct Params {
+    const double *verts;
+    long long n;
+    const double *err;
+    int err_stride;
+    double ms, delta;
+    long long max_itr;
+    unsigned char *collides;
+    double *toi, *out_tol;
+    long long *checks;
+    Header *hdr;
+    int *surv;
+    int *over;
+    double *kappa;
+};
+
+__device__ __forceinline__ void write_result(const Params &p, long long qi, int c, double toi,
+                                             double tol, long long n)
+{
+    p.collides[qi] = (unsigned char)c;
+    p.toi[qi] = toi;
+    p.out_tol[qi] = tol;
+    if (p.checks) p.checks[qi] = n;
+}
+
+// ---- 1. level-0 filter ------------------------------------------------------
+
+template <int KIND>
+__global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
+{
+    const long long i = (long long)blockIdx.x * ROOT_THREADS + threadIdx.x;
+    if (i >= p.n) return;
+    Query Q;
+    load_query(p.verts, p.n, i, Q);
+    double eps[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) eps[c] = __ldg(p.err + (size_t)p.err_stride * i + c);
+
+    // Corners of [0,1]^3.  At t = 0 the position x0 + dx*0 equals x0 and at
+    // t = 1 it is x0 + dx; with u, v in {0, 1} the products u e1, v e2 are
+    // 0 or the factor itself, so these are the fixed-order values of F.
+    double F[2][2][2][3];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        double P[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) P[j] = it ? dadd(Q.x0[j], Q.dx[j]) : Q.x0[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (KIND == CCD_KIND_VF) {
+                double q = dsub(P[c], P[3 + c]);
+                double e1 = dsub(P[6 + c], P[3 + c]);
+                double e2 = dsub(P[9 + c], P[3 + c]);
+                double a1 = dsub(q, e1);
+                F[it][0][0][c] = q;
+                F[it][1][0][c] = a1;
+                F[it][0][1][c] = dsub(q, e2);
+                F[it][1][1][c] = dsub(a1, e2);
+            } else {
+                double d1 = dsub(P[3 + c], P[c]);
+                double d2 = dsub(P[9 + c], P[6 + c]);
+                double a1 = dadd(P[c], d1), b1 = dadd(P[6 + c], d2);
+                F[it][0][0][c] = dsub(P[c], P[6 + c]);
+                F[it][1][0][c] = dsub(a1, P[6 + c]);
+                F[it][0][1][c] = dsub(P[c], b1);
+                F[it][1][1][c] = dsub(a1, b1);
+            }
+        }
+    }
+    double m[3], M[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double lo = F[0][0][0][c], hi = lo;
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            double f = F[k >> 2][(k >> 1) & 1][k & 1][c];
+            lo = fmin(lo, f);
+            hi = fmax(hi, f);
+        }
+        m[c] = lo;
+        M[c] = hi;
+    }
+    BoxTest bt = box_test(m, M, eps, p.ms, p.delta);
+    if (!bt.hit) {
+        write_result(p, i, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0, 1);
+        return;
+    }
+    if (1 >= p.max_itr || bt.term) {      // first colliding box of level 0
+        write_result(p, i, 1, 0.0, bt.w, 1);
+        return;
+    }
+    // Eq. (kappas) over the corners of [0,1]^3.
+    double kt = 0.0, ku = 0.0, kv = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                kt = fmax(kt, fabs(dsub(F[0][a][b][c], F[1][a][b][c])));
+                ku = fmax(ku, fabs(dsub(F[a][0][b][c], F[a][1][b][c])));
+                kv = fmax(kv, fabs(dsub(F[a][b][0][c], F[a][b][1][c])));
+            }
+    p.kappa[3 * i + 0] = dmul(3.0, kt);
+    p.kappa[3 * i + 1] = dmul(3.0, ku);
+    p.kappa[3 * i + 2] = dmul(3.0, kv);
+    // warp-aggregated append to the survivor list
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&p.hdr->survivors, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    p.surv[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
+}
+
+// ---- 2./3. per-query level-synchronous solver --------------------------------
+
+// Runs Algorithm 2 for query qi with BS cooperating threads.  Returns false
+// if a level needed more than `cap` boxes (nothing is written then unless
+// `fallback` is set, in which case the query is answered as at the check
+// limit and the capacity status is recorded).
+//
+// Bound used to size the deep slots: every box of level l+1 is a child of a
+// colliding box of level l whose check index n was below m_I (otherwise the
+// query returned), so a level never holds more than 2 (m_I - 1) boxes.
+template <int KIND, int BS>
+__device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, long long cap,
+                            bool fallback, Smem<BS> &s)
+{
+    const int tid = threadIdx.x;
+    Query Q;
+    load_query(p.verts, p.n, qi, Q);
+    double eps[3], kap[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        eps[c] = __ldg(p.err + (size_t)p.err_stride * qi + c);
+        kap[c] = p.kappa[3 * qi + c];
+    }
+    int k[3] = {0, 0, 0};
+    long long size = 1;
+    if (tid == 0) cur[0] = Box{{0ull, 0ull, 0ull}};
+    bsync<BS>();
+    long long n_before = 0;
+
+    for (;;) {
+        // split(): c_d = w(I_d) kappa_d, ties t > u > v.  Same for the level.
+        const double ct = dmul(pow2neg(k[0]), kap[0]);
+        const double cu = dmul(pow2neg(k[1]), kap[1]);
+        const double cv = dmul(pow2neg(k[2]), kap[2]);
+        double cm = ct;
+        if (cu > cm) cm = cu;
+        if (cv > cm) cm = cv;
+        const int sd = (ct == cm) ? 0 : (cu == cm) ? 1 : 2;
+        const bool can_split = k[sd] < KMAX;
+
+        bool found = false;
+        unsigned long long if_at = 0;
+        double first_w = 0.0;
+        long long ncol = 0;
+        for (long long base = 0; base < size; base += BS) {
+            const long long i = base + tid;
+            const bool valid = i < size;
+            Box b = Box{{0ull, 0ull, 0ull}};
+            BoxTest bt{false, false, 0.0};
+            if (valid) {
+                b = cur[i];
+                double m[3], M[3];
+                box_eval<KIND>(Q, dyadic(b.a[0], k[0]), dyadic(b.a[0] + 1, k[0]),
+                               dyadic(b.a[1], k[1]), dyadic(b.a[1] + 1, k[1]),
+                               dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), m, M);
+                bt = box_test(m, M, eps, p.ms, p.delta);
+            }
+            const long long nb = n_before + i + 1;
+            const int fc = block_min<BS>(bt.hit ? tid : BIG, s);
+            const int cut = block_min<BS>((bt.hit && nb >= p.max_itr) ? tid : BIG, s);
+            if (!found && fc != BIG) {
+                found = true;
+                if (tid == fc) {
+                    s.first_at = b.a[0];
+                    s.first_w = bt.w;
+                    s.first_term = bt.term;
+                }
+                bsync<BS>();
+                if_at = s.first_at;
+                first_w = s.first_w;
+                const bool term = s.first_term;
+                bsync<BS>();
+                const long long nfc = n_before + base + fc + 1;
+                if (nfc >= p.max_itr || term || !can_split) {
+                    if (tid == 0) write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
+                    return true;
+                }
+            }
+            if (cut != BIG) {   // a later colliding box reached the check limit
+                if (tid == cut) s.cut_w = bt.w;
+                bsync<BS>();
+                const double w = s.cut_w;
+                bsync<BS>();
+                if (tid == 0)
+                    write_result(p, qi, 1, dyadic(if_at, k[0]), w, n_before + base + cut + 1);
+                return true;
+            }
+            int total;
+            const int pre = block_excl_scan<BS>(bt.hit ? 1 : 0, &total, s);
+            if (bt.hit) cur[ncol + pre] = b;   // in-place compaction, ncol + pre <= i
+            ncol += total;
+            bsync<BS>();
+        }
+        if (!found) {
+            if (tid == 0)
+                write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
+                             n_before + size);
+            return true;
+        }
+        n_before += size;
+
+        // children of the ncol colliding boxes, in Q order
+        long long nchild;
+        if (sd == 0) {
+            nchild = 2 * ncol;
+            if (nchild <= cap) {
+                long long carry = -1;   // start of the open group of equal I_t
+                for (long long base = 0; base < ncol; base += BS) {
+                    const long long j = base + tid;
+                    const bool valid = j < ncol;
+                    Box b = Box{{0ull, 0ull, 0ull}};
+                    long long v = -1;
+                    if (valid) {
+                        b = cur[j];
+                        if (j == 0 || cur[j - 1].a[0] != b.a[0]) v = j;
+                    }
+                    const long long gs = max(carry, block_incl_maxscan<BS>(v, s));
+                    if (valid) nxt[j + gs] = Box{{2 * b.a[0], b.a[1], b.a[2]}};
+                    carry = max(carry, block_maxl<BS>(v, s));
+                }
+                long long carry_e = ncol;   // end of the open group, scanning backwards
+                const long long last = ((ncol - 1) / BS) * BS;
+                for (long long base = last; base >= 0; base -= BS) {
+                    const long long j = base + tid;
+                    const bool valid = j < ncol;
+                    Box b = Box{{0ull, 0ull, 0ull}};
+                    long long v = BIGL;
+                    if (valid) {
+                        b = cur[j];
+                        if (j + 1 == ncol || cur[j + 1].a[0] != b.a[0]) v = j + 1;
+                    }
+                    const long long ge = min(carry_e, block_suffix_min<BS>(v, s));
+                    if (valid) nxt[j + ge] = Box{{2 * b.a[0] + 1, b.a[1], b.a[2]}};
+                    carry_e = min(carry_e, block_minl<BS>(v, s));
+                }
+            }
+        } else {
+            long long carry = 0;        // right children kept so far
+            for (long long base = 0; base < ncol; base += BS) {
+                const long long j = base + tid;
+                const bool valid = j < ncol;
+                Box b = Box{{0ull, 0ull, 0ull}};
+                bool keep_r = false;
+                if (valid) {
+                    b = cur[j];
+                    keep_r = true;
+                    if (KIND == CCD_KIND_VF) {
+                        // right child meets the prism iff u_L + v_L <= 1 (exact)
+                        const int ku = k[1] + (sd == 1), kv = k[2] + (sd == 2);
+                        const unsigned long long au = sd == 1 ? 2 * b.a[1] + 1 : b.a[1];
+                        const unsigned long long av = sd == 2 ? 2 * b.a[2] + 1 : b.a[2];
+                        const int K = ku > kv ? ku : kv;
+                        keep_r = (au << (K - ku)) + (av << (K - kv)) <= (1ull << K);
+                    }
+                }
+                int total;
+                const int pre = block_excl_scan<BS>(keep_r ? 1 : 0, &total, s);
+                if (valid) {
+                    const long long pos = j + carry + pre;
+                    Box l = b, r = b;
+                    l.a[sd] = 2 * b.a[sd];
+                    r.a[sd] = 2 * b.a[sd] + 1;
+                    if (pos < cap) nxt[pos] = l;
+                    if (keep_r && pos + 1 < cap) nxt[pos + 1] = r;
+                }
+                carry += total;
+            }
+            nchild = ncol + carry;
+        }
+        if (nchild > cap) {
+            if (!fallback) return false;
+            // answered as at the check limit: conservative, flagged
+            if (tid == 0) {
+                write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, n_before);
+                atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
+                atomicAdd(&p.hdr->fallbacks, 1);
+            }
+            return true;
+        }
+        bsync<BS>();
+        Box *t = cur;
+        cur = nxt;
+        nxt = t;
+        size = nchild;
+        k[sd] += 1;
+    }
+}
+
+template <int KIND, int BS>
+__global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slots, long long cap)
+{
+    __shared__ Smem<BS> s;
+    __shared__ int s_idx;
+    Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
+    Box *nxt = cur + cap;
+    const int *list = deep ? p.over : p.surv;
+    const int *count = deep ? &p.hdr->overflow : &p.hdr->survivors;
+    int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(head, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= *(volatile const int *)count) return;
+        const long long qi = list[idx];
+        const bool done = solve_query<KIND, BS>(p, qi, cur, nxt, cap, deep != 0, s);
+        if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
+        __syncthreads();
+    }
+}
+
+// ---- eps from bounds (Eq. ccd-error / msccd-error) ---------------------------
+
+__global__ void err_init_kernel(unsigned long long *g)
+{
+    if (threadIdx.x < 3) g[threadIdx.x] = (unsigned long long)__double_as_longlong(1.0);
+}
+
+// scene-wide: atomicMax on the bit pattern (monotone for non-negative doubles)
+__global__ void err_reduce_kernel(const double *__restrict__ verts, long long n,
+                                  unsigned long long *g)
+{
+    double mx[3] = {0.0, 0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 24; ++k) mx[k % 3] = fmax(mx[k % 3], fabs(verts[(size_t)k * n + i]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double v = mx[c];
+        for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(g + c, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+__global__ void err_finish_kernel(const unsigned long long *g, double K, double *out)
+{
+    if (threadIdx.x < 3) {
+        double gm = __longlong_as_double((long long)g[threadIdx.x]);
+        out[threadIdx.x] = dmul(K, dmul(dmul(gm, gm), gm));
+    }
+}
+
+__global__ void err_per_query_kernel(const double *__restrict__ verts, long long n, double K,
+                                     double *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double g[3] = {1.0, 1.0, 1.0};
+#pragma unroll
+    for (int k = 0; k < 24; ++k) g[k % 3] = fmax(g[k % 3], fabs(verts[(size_t)k * n + i]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[3 * i + c] = dmul(K, dmul(dmul(g[c], g[c]), g[c]));
+}
+
+// ---- FP64 pipe probe ---------------------------------------------------------
+
+__device__ double g_probe_sink;
+
+__global__ void __launch_bounds__(256) fp64_probe_kernel(int iters)
+{
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+    const double b = 0.9999999, c = 1e-7;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = __fma_rn(a[j], b, c);
+    double r = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r += a[j];
+    if (r != r) g_probe_sink = r;   // never true; keeps the chains live
+}
+
+// ---- host side ----------------------------------------------------------------
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+long long deep_cap(long long max_itr) { return 2 * max_itr + 64; }
+
+// Fixed part of the workspace for n queries.
+Layout layout_fixed(long long n, int sms)
+{
+    Layout L{};
+    size_t off = align256(sizeof(Header));
+    L.off_surv = off; off = align256(off + sizeof(int) * (size_t)n);
+    L.off_over = off; off = align256(off + sizeof(int) * (size_t)n);
+    L.off_kappa = off; off = align256(off + 3 * sizeof(double) * (size_t)n);
+    L.nb_small = sms * SMALL_BLOCKS_PER_SM;
+    L.cap_small = SMALL_CAP;
+    L.off_small = off; off = align256(off + sizeof(Box) * 2 * (size_t)SMALL_CAP * L.nb_small);
+    L.off_deep = off;
+    L.total = off;
+    return L;
+}
+
+bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout *out)
+{
+    Layout L = layout_fixed(n, sms);
+    if (ws_bytes < L.off_deep) return false;
+    const size_t room = ws_bytes - L.off_deep;
+    const long long want = deep_cap(max_itr);
+    const size_t per = sizeof(Box) * 2 * (size_t)want;
+    long long nb = (long long)(room / per);
+    if (nb >= 1) {
+        L.nb_deep = (int)(nb < sms ? nb : sms);
+        L.cap_deep = want;
+    } else {
+        L.nb_deep = 1;
+        L.cap_deep = (long long)(room / (sizeof(Box) * 2));
+        if (L.cap_deep < 1024) return false;
+    }
+    L.total = L.off_deep + sizeof(Box) * 2 * (size_t)L.cap_deep * L.nb_deep;
+    *out = L;
+    return true;
+}
+
+template <int KIND>
+ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_stride,
+                     double ms, double delta, int64_t max_itr, uint8_t *collides, double *toi,
+                     double *out_tol, int64_t *checks, void *workspace, size_t ws_bytes,
+                     void *stream)
+{
+    if (n < 0 || n >= 0x7fffffffLL || !(delta > 0.0) || max_itr <= 0 || !(ms >= 0.0) ||
+        (err_stride != 0 && err_stride != 3))
+        return CCD_ERR_ARG;
+    if (n > 0 && (!verts || !err || !collides || !toi || !out_tol)) return CCD_ERR_ARG;
+    if (!workspace) return CCD_ERR_WORKSPACE;
+    const int sms = device_sms();
+    if (sms <= 0) return CCD_ERR_CUDA;
+    Layout L;
+    if (!layout_for(n, max_itr, ws_bytes, sms, &L)) return CCD_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    if (cudaMemsetAsync(ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
+    if (n == 0) return CCD_OK;
+
+    Params p;
+    p.verts = verts; p.n = n; p.err = err; p.err_stride = err_stride;
+    p.ms = ms; p.delta = delta; p.max_itr = max_itr;
+    p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
+    p.hdr = (Header *)ws;
+    p.surv = (int *)(ws + L.off_surv);
+    p.over = (int *)(ws + L.off_over);
+    p.kappa = (double *)(ws + L.off_kappa);
+
+    const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
+    root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
+    solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, 0, st>>>(
+        p, 0, (Box *)(ws + L.off_small), L.cap_small);
+    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, 0, st>>>(
+        p, 1, (Box *)(ws + L.off_deep), L.cap_deep);
+    if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
+    return CCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ccd_workspace_bytes(int64_t n, int64_t max_itr)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr <= 0) return 0;
+    const int sms = device_sms();
+    if (sms <= 0) return 0;
+    Layout L = layout_fixed(n, sms);
+    return L.off_deep + sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)sms;
+}
+
+ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err, int err_stride,
+                        double ms, double delta, int64_t max_itr, uint8_t *collides, double *toi,
+                        double *out_tol, int64_t *checks, void *workspace, size_t ws_bytes,
+                        void *stream)
+{
+    return run_batch<CCD_KIND_VF>(verts, n, err, err_stride, ms, delta, max_itr, collides, toi,
+                                  out_tol, checks, workspace, ws_bytes, stream);
+}
+
+ccd_status ccd_ee_batch(const double *verts, int64_t n, const double *err, int err_stride,
+                        double ms, double delta, int64_t max_itr, uint8_t *collides, double *toi,
+                        double *out_tol, int64_t *checks, void *workspace, size_t ws_bytes,
+                        void *stream)
+{
+    return run_batch<CCD_KIND_EE>(verts, n, err, err_stride, ms, delta, max_itr, collides, toi,
+                                  out_tol, checks, workspace, ws_bytes, stream);
+}
+
+ccd_status ccd_err_from_bounds(int kind, const double *verts, int64_t n, int ms_nonzero,
+                               int per_query, double *err_out, void *stream)
+{
+    if ((kind != CCD_KIND_VF && kind != CCD_KIND_EE) || n < 0 || n >= 0x7fffffffLL || !err_out ||
+        (n > 0 && !verts))
+        return CCD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double K = kind == CCD_KIND_VF ? (ms_nonzero ? 7.549516567451064e-15 : 6.661338147750939e-15)
+                                         : (ms_nonzero ? 7.105427357601002e-15 : 6.217248937900877e-15);
+    if (per_query) {
+        if (n > 0)
+            err_per_query_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(verts, n, K, err_out);
+    } else {
+        // the 3 output doubles double as the reduction scratch
+        unsigned long long *g = (unsigned long long *)err_out;
+        err_init_kernel<<<1, 32, 0, st>>>(g);
+        if (n > 0) {
+            const int sms = device_sms();
+            long long blocks = (n + 255) / 256;
+            if (blocks > 8LL * sms) blocks = 8LL * sms;
+            err_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, n, g);
+        }
+        err_finish_kernel<<<1, 32, 0, st>>>(g, K, err_out);
+    }
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t *fallbacks,
+                                void *stream)
+{
+    if (!workspace || !status) return CCD_ERR_ARG;
+    Header h;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, workspace, sizeof(Header), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return CCD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCD_ERR_CUDA;
+    *status = h.status;
+    if (fallbacks) *fallbacks = h.fallbacks;
+    return CCD_OK;
+}
+
+const char *ccd_status_str(int status)
+{
+    switch (status) {
+    case CCD_OK: return "ok";
+    case CCD_ERR_ARG: return "invalid argument";
+    case CCD_ERR_WORKSPACE: return "workspace missing or too small";
+    case CCD_ERR_TIMEOUT: return "bounded device wait gave up";
+    case CCD_ERR_CUDA: return "CUDA launch or copy failed";
+    case CCD_ERR_CAPACITY: return "frontier exceeded its slot; conservative fallback used";
+    default: return "unknown status";
+    }
+}
+
+ccd_status ccd_fp64_peak_probe(int blocks, int iters, float *ms_out, void *stream)
+{
+    if (blocks <= 0 || iters <= 0 || !ms_out) return CCD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CCD_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return CCD_ERR_CUDA; }
+    fp64_probe_kernel<<<blocks, 256, 0, st>>>(iters);   // warm-up
+    cudaEventRecord(e0, st);
+    fp64_probe_kernel<<<blocks, 256, 0, st>>>(iters);
+    cudaEventRecord(e1, st);
+    ccd_status r = CCD_OK;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms_out, e0, e1) != cudaSuccess)
+        r = CCD_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) r = CCD_ERR_CUDA;
+    return r;
+}
+
+}  // extern "C"
