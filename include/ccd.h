@@ -51,9 +51,10 @@ typedef enum {
 /*
  * Bytes of device workspace that ccd_vf_batch / ccd_ee_batch need for n
  * queries at check limit max_itr with the default number of deep slots (one
- * per SM of the current device).  A smaller workspace is accepted as long as
- * it holds at least one deep slot; fewer slots only reduce parallelism on
- * queries with very large subdivision frontiers.  Returns 0 on bad arguments.
+ * per SM of the current device).  One deep slot takes 48 * (2 * max_itr + 64)
+ * bytes.  A smaller workspace is accepted as long as it holds at least one
+ * deep slot; fewer slots only reduce parallelism on queries with very large
+ * subdivision frontiers.  Returns 0 on bad arguments or without a device.
  */
 size_t ccd_workspace_bytes(int64_t n, int64_t max_itr);
 
@@ -127,6 +128,26 @@ ccd_status ccd_err_from_bounds(int kind, const double *verts, int64_t n,
  */
 ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
                                 int32_t *fallbacks, void *stream);
+
+/*
+ * Counters of the last batch that used `workspace` (synchronizes `stream`):
+ * [0] queries that survived the level-0 check, [1] queries moved to the deep
+ * solver, [2] capacity fallbacks, [3] sum of check counts n of queries
+ * finished by the small-frontier solver, [4] the same for the deep solver,
+ * [5] box evaluations executed by the small-frontier solver (including work
+ * of queries it handed on), [6] the same for the deep solver, [7] status.
+ */
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[8], void *stream);
+
+/*
+ * Optional stage timing for benchmarks: with count == 4, every following
+ * batch call records events[0] before the level-0 kernel, events[1] after
+ * it, events[2] after the small-frontier solver and events[3] after the
+ * deep solver, on the call's stream.  The events (cudaEvent_t, created by
+ * the caller) are not retained beyond the next ccd_set_stage_events call;
+ * count == 0 switches recording off.  Process-wide; not thread-safe.
+ */
+ccd_status ccd_set_stage_events(void *const *events, int count);
 
 /* Static description of a status code. */
 const char *ccd_status_str(int status);

@@ -50,6 +50,10 @@ def lib():
         L.ccd_workspace_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), vp]
         L.ccd_workspace_status.restype = ctypes.c_int
+        L.ccd_workspace_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.ccd_workspace_counters.restype = ctypes.c_int
+        L.ccd_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        L.ccd_set_stage_events.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
         L.ccd_status_str.restype = ctypes.c_char_p
         L.ccd_fp64_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -85,11 +89,22 @@ def workspace_bytes(n: int, max_itr: int) -> int:
     return int(lib().ccd_workspace_bytes(int(n), int(max_itr)))
 
 
-def workspace(n: int, max_itr: int, device=None) -> torch.Tensor:
-    """Caller-owned device workspace for ``n`` queries at check limit ``max_itr``."""
+def deep_slot_bytes(max_itr: int) -> int:
+    """Bytes of one deep-solver slot: two frontiers of 2*max_itr + 64 boxes of
+    24 bytes (the layout documented with ccd_workspace_bytes)."""
+    return 2 * (2 * int(max_itr) + 64) * 24
+
+
+def workspace(n: int, max_itr: int, device=None, deep_slots: int | None = None) -> torch.Tensor:
+    """Caller-owned device workspace for ``n`` queries at check limit
+    ``max_itr``; ``deep_slots`` caps the deep-solver slots (default: one per SM)."""
     nbytes = workspace_bytes(n, max_itr)
     if nbytes == 0:
         raise CCDError(-1, "ccd_workspace_bytes")
+    if deep_slots is not None:
+        dev = torch.device(device or "cuda")
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        nbytes -= max(0, sms - int(deep_slots)) * deep_slot_bytes(max_itr)
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
@@ -154,6 +169,26 @@ def workspace_status(ws: torch.Tensor, stream=None):
     _check(lib().ccd_workspace_status(_ptr(ws), ctypes.byref(st), ctypes.byref(fb),
                                       _stream(stream)), "ccd_workspace_status")
     return st.value, fb.value
+
+
+COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
+                 "evals_small", "evals_deep", "status")
+
+
+def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
+    arr = (ctypes.c_int64 * 8)()
+    _check(lib().ccd_workspace_counters(_ptr(ws), arr, _stream(stream)), "ccd_workspace_counters")
+    return dict(zip(COUNTER_NAMES, list(arr)))
+
+
+def set_stage_events(events) -> None:
+    """events: None (off) or 4 torch.cuda.Event(enable_timing=True), each
+    already recorded once (so that its CUDA handle exists)."""
+    if not events:
+        _check(lib().ccd_set_stage_events(None, 0), "ccd_set_stage_events")
+        return
+    arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(lib().ccd_set_stage_events(arr, 4), "ccd_set_stage_events")
 
 
 def fp64_peak_probe(blocks: int, iters: int, stream=None):

@@ -61,7 +61,12 @@ struct Header {
     int head_deep;   // work counter of the deep solver
     int status;      // CCD_OK or CCD_ERR_CAPACITY
     int fallbacks;   // queries answered by the capacity fallback
-    int pad[58];
+    int pad0[2];
+    unsigned long long checks_small;  // sum of n over queries finished by the small solver
+    unsigned long long checks_deep;   // sum of n over queries finished by the deep solver
+    unsigned long long evals_small;   // box evaluations executed by the small solver
+    unsigned long long evals_deep;    // box evaluations executed by the deep solver
+    int pad[48];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -457,11 +462,19 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
 // Bound used to size the deep slots: every box of level l+1 is a child of a
 // colliding box of level l whose check index n was below m_I (otherwise the
 // query returned), so a level never holds more than 2 (m_I - 1) boxes.
+__device__ __forceinline__ void count_done(const Params &p, bool deep, long long n,
+                                           unsigned long long evals)
+{
+    atomicAdd(deep ? &p.hdr->checks_deep : &p.hdr->checks_small, (unsigned long long)n);
+    atomicAdd(deep ? &p.hdr->evals_deep : &p.hdr->evals_small, evals);
+}
+
 template <int KIND, int BS>
 __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, long long cap,
                             bool fallback, Smem<BS> &s)
 {
     const int tid = threadIdx.x;
+    unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
     Query Q;
     load_query(p.verts, p.n, qi, Q);
     double eps[3], kap[3];
@@ -504,6 +517,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                                dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), m, M);
                 bt = box_test(m, M, eps, p.ms, p.delta);
             }
+            evals += (unsigned long long)min((long long)BS, size - base);
             const long long nb = n_before + i + 1;
             const int fc = block_min<BS>(bt.hit ? tid : BIG, s);
             const int cut = block_min<BS>((bt.hit && nb >= p.max_itr) ? tid : BIG, s);
@@ -521,7 +535,10 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 bsync<BS>();
                 const long long nfc = n_before + base + fc + 1;
                 if (nfc >= p.max_itr || term || !can_split) {
-                    if (tid == 0) write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
+                    if (tid == 0) {
+                        write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
+                        count_done(p, fallback, nfc, evals);
+                    }
                     return true;
                 }
             }
@@ -530,8 +547,10 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 bsync<BS>();
                 const double w = s.cut_w;
                 bsync<BS>();
-                if (tid == 0)
+                if (tid == 0) {
                     write_result(p, qi, 1, dyadic(if_at, k[0]), w, n_before + base + cut + 1);
+                    count_done(p, fallback, n_before + base + cut + 1, evals);
+                }
                 return true;
             }
             int total;
@@ -541,9 +560,11 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
             bsync<BS>();
         }
         if (!found) {
-            if (tid == 0)
+            if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
+                count_done(p, fallback, n_before + size, evals);
+            }
             return true;
         }
         n_before += size;
@@ -617,12 +638,16 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
             nchild = ncol + carry;
         }
         if (nchild > cap) {
-            if (!fallback) return false;
+            if (!fallback) {
+                if (tid == 0) atomicAdd(&p.hdr->evals_small, evals);
+                return false;
+            }
             // answered as at the check limit: conservative, flagged
             if (tid == 0) {
                 write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
+                count_done(p, true, n_before, evals);
             }
             return true;
         }
@@ -770,6 +795,14 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
     return true;
 }
 
+cudaEvent_t g_stage_events[4];
+int g_stage_events_on = 0;
+
+inline void stage_mark(int i, cudaStream_t st)
+{
+    if (g_stage_events_on) cudaEventRecord(g_stage_events[i], st);
+}
+
 template <int KIND>
 ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_stride,
                      double ms, double delta, int64_t max_itr, uint8_t *collides, double *toi,
@@ -800,11 +833,15 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     p.kappa = (double *)(ws + L.off_kappa);
 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
+    stage_mark(0, st);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
+    stage_mark(1, st);
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, 0, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small);
+    stage_mark(2, st);
     solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, 0, st>>>(
         p, 1, (Box *)(ws + L.off_deep), L.cap_deep);
+    stage_mark(3, st);
     if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
     return CCD_OK;
 }
@@ -878,6 +915,40 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t 
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCD_ERR_CUDA;
     *status = h.status;
     if (fallbacks) *fallbacks = h.fallbacks;
+    return CCD_OK;
+}
+
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[8], void *stream)
+{
+    if (!workspace || !counters) return CCD_ERR_ARG;
+    Header h;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, workspace, sizeof(Header), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return CCD_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCD_ERR_CUDA;
+    counters[0] = h.survivors;
+    counters[1] = h.overflow;
+    counters[2] = h.fallbacks;
+    counters[3] = (int64_t)h.checks_small;
+    counters[4] = (int64_t)h.checks_deep;
+    counters[5] = (int64_t)h.evals_small;
+    counters[6] = (int64_t)h.evals_deep;
+    counters[7] = h.status;
+    return CCD_OK;
+}
+
+ccd_status ccd_set_stage_events(void *const *events, int count)
+{
+    if (count == 0) {
+        g_stage_events_on = 0;
+        return CCD_OK;
+    }
+    if (count != 4 || !events) return CCD_ERR_ARG;
+    for (int i = 0; i < 4; ++i) {
+        if (!events[i]) return CCD_ERR_ARG;
+        g_stage_events[i] = (cudaEvent_t)events[i];
+    }
+    g_stage_events_on = 1;
     return CCD_OK;
 }
 
