@@ -120,41 +120,130 @@ __device__ __forceinline__ void load_query(const double *__restrict__ verts, lon
     }
 }
 
-// B_F(I) of Eq. (box): per-axis min m and max M of F over the 8 corners.
-template <int KIND>
-__device__ __forceinline__ void box_eval(const Query &Q, double tl, double tr, double ul,
-                                         double ur, double vl, double vr, double (&m)[3],
-                                         double (&M)[3])
+// ---- order-preserving integer keys of doubles --------------------------------
+// On GB300 FP64 min/max/compare issue on the same scarce FP64 pipe as add and
+// multiply, so the box test orders doubles through integer keys instead:
+// key(x) flips the magnitude bits of negative x, making signed 64-bit order
+// equal to numeric order for finite x (only -0 < +0 differs from IEEE, which
+// the thresholds below absorb).
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+// thresholds: x <= c  <=>  dkey(x) <= key_le(c);  x >= c  <=>  dkey(x) >= key_ge(c)
+__device__ __forceinline__ long long key_le(double c) { return c == 0.0 ? 0LL : dkey(c); }
+__device__ __forceinline__ long long key_ge(double c) { return c == 0.0 ? -1LL : dkey(c); }
+
+struct Thresholds {
+    long long le_eps[3];   // x <= eps_c
+    long long ge_neps[3];  // x >= -eps_c
+    long long delta;       // w < delta (w >= +0, delta > 0)
+};
+
+__device__ __forceinline__ void make_thresholds(const double (&eps)[3], double delta,
+                                                Thresholds &T)
 {
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double t = it ? tr : tl;
-        double P[12];
+    for (int c = 0; c < 3; ++c) {
+        T.le_eps[c] = key_le(eps[c]);
+        T.ge_neps[c] = key_ge(-eps[c]);
+    }
+    T.delta = dkey(delta);
+}
+
+// Quantities of F that depend on t only, for one value of t (fixed order):
+// VF: q = p - v1, e1 = v2 - v1, e2 = v3 - v1;  EE: p1, d1 = p2 - p1, p3, d2 = p4 - p3.
+template <int KIND>
+struct TWidth { static constexpr int W = KIND == CCD_KIND_VF ? 9 : 12; };
+
+template <int KIND>
+__device__ __forceinline__ void t_quantities(const Query &Q, double t, double *out)
+{
+    double P[12];
 #pragma unroll
-        for (int j = 0; j < 12; ++j) P[j] = dadd(Q.x0[j], dmul(Q.dx[j], t));
+    for (int j = 0; j < 12; ++j) P[j] = dadd(Q.x0[j], dmul(Q.dx[j], t));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (KIND == CCD_KIND_VF) {
+            out[c] = dsub(P[c], P[3 + c]);
+            out[3 + c] = dsub(P[6 + c], P[3 + c]);
+            out[6 + c] = dsub(P[9 + c], P[3 + c]);
+        } else {
+            out[c] = P[c];
+            out[3 + c] = dsub(P[3 + c], P[c]);
+            out[6 + c] = P[6 + c];
+            out[9 + c] = dsub(P[9 + c], P[6 + c]);
+        }
+    }
+}
+
+// B_F(I) from the t-quantities of t_L (TL) and t_R (TR): per-axis integer
+// keys of the min and max over the 8 corners.
+template <int KIND>
+__device__ __forceinline__ void corners_keys(const double *TL, const double *TR, double ul,
+                                             double ur, double vl, double vr, long long (&km)[3],
+                                             long long (&kM)[3])
+{
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const double *T = side ? TR : TL;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double f0, f1, f2, f3;
             if (KIND == CCD_KIND_VF) {
-                double q = dsub(P[c], P[3 + c]);
-                double e1 = dsub(P[6 + c], P[3 + c]);
-                double e2 = dsub(P[9 + c], P[3 + c]);
-                double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
-                double bl = dmul(vl, e2), br = dmul(vr, e2);
+                const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
+                const double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
+                const double bl = dmul(vl, e2), br = dmul(vr, e2);
                 f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
             } else {
-                double d1 = dsub(P[3 + c], P[c]);
-                double d2 = dsub(P[9 + c], P[6 + c]);
-                double al = dadd(P[c], dmul(ul, d1)), ar = dadd(P[c], dmul(ur, d1));
-                double bl = dadd(P[6 + c], dmul(vl, d2)), br = dadd(P[6 + c], dmul(vr, d2));
+                const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
+                const double al = dadd(a, dmul(ul, d1)), ar = dadd(a, dmul(ur, d1));
+                const double bl = dadd(b, dmul(vl, d2)), br = dadd(b, dmul(vr, d2));
                 f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
             }
-            double lo = fmin(fmin(f0, f1), fmin(f2, f3));
-            double hi = fmax(fmax(f0, f1), fmax(f2, f3));
-            if (it == 0) { m[c] = lo; M[c] = hi; }
-            else { m[c] = fmin(m[c], lo); M[c] = fmax(M[c], hi); }
+            const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
+            const long long lo = min(min(k0, k1), min(k2, k3));
+            const long long hi = max(max(k0, k1), max(k2, k3));
+            if (side == 0) { km[c] = lo; kM[c] = hi; }
+            else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
         }
     }
+}
+
+// The box test of Algorithm 2 on integer keys (Sec. 5.1 enlargement by ms).
+__device__ __forceinline__ void box_test_keys(const long long (&km)[3], const long long (&kM)[3],
+                                              const Thresholds &T, double ms, bool &hit,
+                                              bool &term, double &w)
+{
+    long long lo[3], hi[3];
+    double wmax = 0.0;
+    long long kw = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double m = dkey_inv(km[c]), M = dkey_inv(kM[c]);
+        const double wc = dsub(M, m);           // >= +0
+        const long long kc = __double_as_longlong(wc);
+        if (c == 0 || kc > kw) { kw = kc; wmax = wc; }
+        if (ms != 0.0) {
+            lo[c] = dkey(dsub(m, ms));
+            hi[c] = dkey(dadd(M, ms));
+        } else {
+            lo[c] = km[c];
+            hi[c] = kM[c];
+        }
+    }
+    hit = (lo[0] <= T.le_eps[0]) & (hi[0] >= T.ge_neps[0]) & (lo[1] <= T.le_eps[1]) &
+          (hi[1] >= T.ge_neps[1]) & (lo[2] <= T.le_eps[2]) & (hi[2] >= T.ge_neps[2]);
+    const bool inside = (lo[0] >= T.ge_neps[0]) & (hi[0] <= T.le_eps[0]) &
+                        (lo[1] >= T.ge_neps[1]) & (hi[1] <= T.le_eps[1]) &
+                        (lo[2] >= T.ge_neps[2]) & (hi[2] <= T.le_eps[2]);
+    term = (kw < T.delta) | inside;
+    w = wmax;
 }
 
 // The box test of Algorithm 2 with the Sec. 5.1 enlargement by ms.
@@ -214,6 +303,8 @@ __device__ __forceinline__ long long warp_maxl(long long v)
 
 template <int BS>
 struct Smem {
+    unsigned long long at[BS];       // a_t of each thread's box in the chunk
+    unsigned long long run_at[BS];   // a_t of each run of equal t_L
     int ired[BS / 32 + 1];
     long long lred[BS / 32 + 1];
     unsigned long long first_at;
@@ -471,7 +562,7 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 
 template <int KIND, int BS>
 __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, long long cap,
-                            bool fallback, Smem<BS> &s)
+                            bool fallback, Smem<BS> &s, double *tq)
 {
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
@@ -483,6 +574,9 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
         eps[c] = __ldg(p.err + (size_t)p.err_stride * qi + c);
         kap[c] = p.kappa[3 * qi + c];
     }
+    Thresholds TH;
+    make_thresholds(eps, p.delta, TH);
+    constexpr int W = TWidth<KIND>::W;
     int k[3] = {0, 0, 0};
     long long size = 1;
     if (tid == 0) cur[0] = Box{{0ull, 0ull, 0ull}};
@@ -509,13 +603,26 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
             const bool valid = i < size;
             Box b = Box{{0ull, 0ull, 0ull}};
             BoxTest bt{false, false, 0.0};
+            if (valid) b = cur[i];
+            // Boxes are in Q order, so equal t_L form contiguous runs: the
+            // t-quantities at t_L and t_R are computed once per run.
+            s.at[tid] = valid ? b.a[0] : ~0ull;
+            bsync<BS>();
+            const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
+            int nrun;
+            const int before = block_excl_scan<BS>(start ? 1 : 0, &nrun, s);
+            const int run = before + (start ? 0 : -1);
+            if (start) s.run_at[before] = b.a[0];
+            bsync<BS>();
+            for (int task = tid; task < 2 * nrun; task += BS)
+                t_quantities<KIND>(Q, dyadic(s.run_at[task >> 1] + (task & 1), k[0]), tq + task * W);
+            bsync<BS>();
             if (valid) {
-                b = cur[i];
-                double m[3], M[3];
-                box_eval<KIND>(Q, dyadic(b.a[0], k[0]), dyadic(b.a[0] + 1, k[0]),
-                               dyadic(b.a[1], k[1]), dyadic(b.a[1] + 1, k[1]),
-                               dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), m, M);
-                bt = box_test(m, M, eps, p.ms, p.delta);
+                long long km[3], kM[3];
+                corners_keys<KIND>(tq + (2 * run) * W, tq + (2 * run + 1) * W,
+                                   dyadic(b.a[1], k[1]), dyadic(b.a[1] + 1, k[1]),
+                                   dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), km, kM);
+                box_test_keys(km, kM, TH, p.ms, bt.hit, bt.term, bt.w);
             }
             evals += (unsigned long long)min((long long)BS, size - base);
             const long long nb = n_before + i + 1;
@@ -665,6 +772,7 @@ __global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slot
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
+    extern __shared__ double tq[];   // [2 * BS][TWidth<KIND>::W] t-quantities
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
     const int *list = deep ? p.over : p.surv;
@@ -677,7 +785,7 @@ __global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slot
         __syncthreads();
         if (idx >= *(volatile const int *)count) return;
         const long long qi = list[idx];
-        const bool done = solve_query<KIND, BS>(p, qi, cur, nxt, cap, deep != 0, s);
+        const bool done = solve_query<KIND, BS>(p, qi, cur, nxt, cap, deep != 0, s, tq);
         if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
         __syncthreads();
     }
@@ -836,10 +944,16 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     stage_mark(0, st);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
-    solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, 0, st>>>(
+    const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
+    const size_t tq_deep = sizeof(double) * 2 * DEEP_THREADS * TWidth<KIND>::W;
+    if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
+        cudaSuccess)
+        return CCD_ERR_CUDA;
+    solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small);
     stage_mark(2, st);
-    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, 0, st>>>(
+    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, tq_deep, st>>>(
         p, 1, (Box *)(ws + L.off_deep), L.cap_deep);
     stage_mark(3, st);
     if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
