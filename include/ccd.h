@@ -135,9 +135,12 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * solver, [2] capacity fallbacks, [3] sum of check counts n of queries
  * finished by the small-frontier solver, [4] the same for the deep solver,
  * [5] box evaluations executed by the small-frontier solver (including work
- * of queries it handed on), [6] the same for the deep solver, [7] status.
+ * of queries it handed on), [6] the same for the deep solver, [7] status,
+ * [8] t-quantity evaluations (positions and edge vectors at one t, shared by
+ * a run of boxes with equal t_L) by the small-frontier solver, [9] the same
+ * for the deep solver.
  */
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[8], void *stream);
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], void *stream);
 
 /*
  * Optional stage timing for benchmarks: with count == 4, every following

@@ -172,11 +172,11 @@ def workspace_status(ws: torch.Tensor, stream=None):
 
 
 COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
-                 "evals_small", "evals_deep", "status")
+                 "evals_small", "evals_deep", "status", "tq_small", "tq_deep")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
-    arr = (ctypes.c_int64 * 8)()
+    arr = (ctypes.c_int64 * 10)()
     _check(lib().ccd_workspace_counters(_ptr(ws), arr, _stream(stream)), "ccd_workspace_counters")
     return dict(zip(COUNTER_NAMES, list(arr)))
 

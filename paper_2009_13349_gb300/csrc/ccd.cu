@@ -66,7 +66,9 @@ struct Header {
     unsigned long long checks_deep;   // sum of n over queries finished by the deep solver
     unsigned long long evals_small;   // box evaluations executed by the small solver
     unsigned long long evals_deep;    // box evaluations executed by the deep solver
-    int pad[48];
+    unsigned long long tq_small;      // t-quantity evaluations by the small solver
+    unsigned long long tq_deep;       // t-quantity evaluations by the deep solver
+    int pad[44];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -164,6 +166,7 @@ struct TWidth { static constexpr int W = KIND == CCD_KIND_VF ? 9 : 12; };
 template <int KIND>
 __device__ __forceinline__ void t_quantities(const Query &Q, double t, double *out)
 {
+    // Q lives in shared memory (one copy per block)
     double P[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) P[j] = dadd(Q.x0[j], dmul(Q.dx[j], t));
@@ -303,6 +306,7 @@ __device__ __forceinline__ long long warp_maxl(long long v)
 
 template <int BS>
 struct Smem {
+    Query query;                     // the query being solved
     unsigned long long at[BS];       // a_t of each thread's box in the chunk
     unsigned long long run_at[BS];   // a_t of each run of equal t_L
     int ired[BS / 32 + 1];
@@ -554,10 +558,11 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
 // colliding box of level l whose check index n was below m_I (otherwise the
 // query returned), so a level never holds more than 2 (m_I - 1) boxes.
 __device__ __forceinline__ void count_done(const Params &p, bool deep, long long n,
-                                           unsigned long long evals)
+                                           unsigned long long evals, unsigned long long tqs)
 {
     atomicAdd(deep ? &p.hdr->checks_deep : &p.hdr->checks_small, (unsigned long long)n);
     atomicAdd(deep ? &p.hdr->evals_deep : &p.hdr->evals_small, evals);
+    atomicAdd(deep ? &p.hdr->tq_deep : &p.hdr->tq_small, tqs);
 }
 
 template <int KIND, int BS>
@@ -566,8 +571,14 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
 {
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
-    Query Q;
-    load_query(p.verts, p.n, qi, Q);
+    unsigned long long tqs = 0;     // t-quantity evaluations (thread 0's tally)
+    Query &Q = s.query;             // shared: only the per-run tasks read it
+    if (tid < 12) {
+        const double a = __ldg(p.verts + (size_t)tid * p.n + qi);
+        const double b = __ldg(p.verts + (size_t)(12 + tid) * p.n + qi);
+        Q.x0[tid] = a;
+        Q.dx[tid] = dsub(b, a);
+    }
     double eps[3], kap[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -614,6 +625,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
             const int run = before + (start ? 0 : -1);
             if (start) s.run_at[before] = b.a[0];
             bsync<BS>();
+            tqs += 2 * (unsigned long long)nrun;
             for (int task = tid; task < 2 * nrun; task += BS)
                 t_quantities<KIND>(Q, dyadic(s.run_at[task >> 1] + (task & 1), k[0]), tq + task * W);
             bsync<BS>();
@@ -644,7 +656,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 if (nfc >= p.max_itr || term || !can_split) {
                     if (tid == 0) {
                         write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
-                        count_done(p, fallback, nfc, evals);
+                        count_done(p, fallback, nfc, evals, tqs);
                     }
                     return true;
                 }
@@ -656,7 +668,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 bsync<BS>();
                 if (tid == 0) {
                     write_result(p, qi, 1, dyadic(if_at, k[0]), w, n_before + base + cut + 1);
-                    count_done(p, fallback, n_before + base + cut + 1, evals);
+                    count_done(p, fallback, n_before + base + cut + 1, evals, tqs);
                 }
                 return true;
             }
@@ -670,7 +682,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
             if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
-                count_done(p, fallback, n_before + size, evals);
+                count_done(p, fallback, n_before + size, evals, tqs);
             }
             return true;
         }
@@ -746,7 +758,10 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
         }
         if (nchild > cap) {
             if (!fallback) {
-                if (tid == 0) atomicAdd(&p.hdr->evals_small, evals);
+                if (tid == 0) {
+                    atomicAdd(&p.hdr->evals_small, evals);
+                    atomicAdd(&p.hdr->tq_small, tqs);
+                }
                 return false;
             }
             // answered as at the check limit: conservative, flagged
@@ -754,7 +769,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
-                count_done(p, true, n_before, evals);
+                count_done(p, true, n_before, evals, tqs);
             }
             return true;
         }
@@ -1032,7 +1047,7 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t 
     return CCD_OK;
 }
 
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[8], void *stream)
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], void *stream)
 {
     if (!workspace || !counters) return CCD_ERR_ARG;
     Header h;
@@ -1048,6 +1063,8 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[8], vo
     counters[5] = (int64_t)h.evals_small;
     counters[6] = (int64_t)h.evals_deep;
     counters[7] = h.status;
+    counters[8] = (int64_t)h.tq_small;
+    counters[9] = (int64_t)h.tq_deep;
     return CCD_OK;
 }
 
