@@ -152,6 +152,34 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], v
  */
 ccd_status ccd_set_stage_events(void *const *events, int count);
 
+/*
+ * Vertex-face batch that allocates nothing (the paper has no counterpart;
+ * this is a deployment variant of ccd_vf_batch).
+ *
+ * For callers that cannot allocate device memory: code running while a CUDA
+ * graph is captured on its stream, real-time loops that must not enter the
+ * allocator, plugins inside a host application that owns every allocation,
+ * processes under a fixed device-memory quota.  Instead of a caller
+ * workspace it uses a 40 MiB file-scope device array that every GPU loading
+ * this library holds until the process exits.  Inputs and outputs are as for
+ * ccd_vf_batch and still come from the caller; results are identical to
+ * ccd_vf_batch's for the same arguments.
+ *
+ * Limits: n <= 32768 queries and max_itr <= 65536 per call; larger requests
+ * return CCD_ERR_WORKSPACE without doing any work.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * The array keeps the last call's contents and every call shares it: the
+ * counters it needs zeroed are cleared on the stream at the start of each
+ * call, and calls that may overlap on the GPU (different streams, or
+ * concurrent host threads) race with each other and must be serialized by
+ * the caller.  No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const double *err,
+                               int err_stride, double ms, double delta, int64_t max_itr,
+                               uint8_t *collides, double *toi, double *out_tol,
+                               int64_t *checks, void *stream);
+
 /* Static description of a status code. */
 const char *ccd_status_str(int status);
 

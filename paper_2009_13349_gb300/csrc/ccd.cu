@@ -1117,3 +1117,113 @@ ccd_status ccd_fp64_peak_probe(int blocks, int iters, float *ms_out, void *strea
 }
 
 }  // extern "C"
+
+// ---- vertex-face batch on a static scratch array (no allocation) -------------
+//
+// For callers that cannot allocate device memory at all: code that runs
+// while a CUDA graph is being captured on its stream, real-time loops that
+// must not enter the driver's allocator, plugins running inside a host that
+// owns every allocation, or processes under a fixed device-memory quota.
+// They get one entry point whose scratch is a file-scope device array that
+// exists on every GPU that loads this library, until the process exits.
+// Its size bounds the batch: at most STATIC_MAX_N queries and a check limit
+// of at most STATIC_MAX_ITR per call.
+
+#include <mutex>
+
+namespace {
+
+constexpr long long STATIC_MAX_N = 32768;
+constexpr long long STATIC_MAX_ITR = 65536;
+constexpr int STATIC_SMALL_BLOCKS = 608;
+constexpr long long STATIC_SMALL_CAP = 256;
+constexpr int STATIC_DEEP_SLOTS = 4;
+constexpr long long STATIC_DEEP_CAP = 2 * STATIC_MAX_ITR + 64;
+
+constexpr size_t st_al(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t STATIC_OFF_SURV = st_al(sizeof(Header));
+constexpr size_t STATIC_OFF_OVER = st_al(STATIC_OFF_SURV + sizeof(int) * STATIC_MAX_N);
+constexpr size_t STATIC_OFF_KAPPA = st_al(STATIC_OFF_OVER + sizeof(int) * STATIC_MAX_N);
+constexpr size_t STATIC_OFF_SMALL = st_al(STATIC_OFF_KAPPA + 3 * sizeof(double) * STATIC_MAX_N);
+constexpr size_t STATIC_OFF_DEEP =
+    st_al(STATIC_OFF_SMALL + sizeof(Box) * 2 * STATIC_SMALL_CAP * STATIC_SMALL_BLOCKS);
+constexpr size_t STATIC_END = STATIC_OFF_DEEP + sizeof(Box) * 2 * STATIC_DEEP_CAP * STATIC_DEEP_SLOTS;
+
+}  // namespace
+
+// 40 MiB on every device that loads the library.
+#define CCD_STATIC_SCRATCH_BYTES (40u << 20)
+static __device__ __align__(256) unsigned char g_static_scratch[CCD_STATIC_SCRATCH_BYTES];
+static_assert(STATIC_END <= CCD_STATIC_SCRATCH_BYTES, "static layout must fit the scratch array");
+
+namespace {
+
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[STATIC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device.  The array's
+// host-side name is only a stand-in for the symbol; the device address comes
+// from cudaGetSymbolAddress, once per device, with that device current.
+char *static_scratch(ccd_status *why)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES) {
+        *why = CCD_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            *why = CCD_ERR_CUDA;
+            return nullptr;
+        }
+        g_static_ptr[dev] = p;
+    }
+    return (char *)g_static_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const double *err,
+                                          int err_stride, double ms, double delta,
+                                          int64_t max_itr, uint8_t *collides, double *toi,
+                                          double *out_tol, int64_t *checks, void *stream)
+{
+    if (n < 0 || !(delta > 0.0) || max_itr <= 0 || !(ms >= 0.0) ||
+        (err_stride != 0 && err_stride != 3))
+        return CCD_ERR_ARG;
+    if (n > 0 && (!verts || !err || !collides || !toi || !out_tol)) return CCD_ERR_ARG;
+    if (n > STATIC_MAX_N || max_itr > STATIC_MAX_ITR) return CCD_ERR_WORKSPACE;
+    ccd_status why = CCD_OK;
+    char *ws = static_scratch(&why);
+    if (!ws) return why;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the counters at the front of the scratch must start at zero each call
+    if (cudaMemsetAsync(ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
+    if (n == 0) return CCD_OK;
+
+    Params p;
+    p.verts = verts; p.n = n; p.err = err; p.err_stride = err_stride;
+    p.ms = ms; p.delta = delta; p.max_itr = max_itr;
+    p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
+    p.hdr = (Header *)ws;
+    p.surv = (int *)(ws + STATIC_OFF_SURV);
+    p.over = (int *)(ws + STATIC_OFF_OVER);
+    p.kappa = (double *)(ws + STATIC_OFF_KAPPA);
+
+    const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
+    root_kernel<CCD_KIND_VF><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
+    const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_VF>::W;
+    const size_t tq_deep = sizeof(double) * 2 * DEEP_THREADS * TWidth<CCD_KIND_VF>::W;
+    if (cudaFuncSetAttribute(solve_kernel<CCD_KIND_VF, DEEP_THREADS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
+        cudaSuccess)
+        return CCD_ERR_CUDA;
+    solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<STATIC_SMALL_BLOCKS, SMALL_THREADS, tq_small, st>>>(
+        p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP);
+    solve_kernel<CCD_KIND_VF, DEEP_THREADS><<<STATIC_DEEP_SLOTS, DEEP_THREADS, tq_deep, st>>>(
+        p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP);
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
