@@ -153,6 +153,69 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], v
 ccd_status ccd_set_stage_events(void *const *events, int count);
 
 /*
+ * Multi-instance batches.  Queries of many simulation instances share one
+ * call: the query array is split into segments, each with its own kind,
+ * tolerances and check limit (Sec. 6 computes eps per scene, and a line
+ * search calls CCD with its own delta, d and m_I per step).  A segment
+ * covers queries [offset, offset + count) of verts; the segments of a call
+ * must tile [0, n) in order (segment s + 1 starts where s ends).
+ */
+typedef struct {
+    int64_t offset;   /* first query of the segment                          */
+    int64_t count;    /* number of queries (>= 0)                            */
+    int32_t kind;     /* CCD_KIND_VF or CCD_KIND_EE                          */
+    int32_t reserved; /* must be 0                                          */
+    double err[3];    /* eps per axis for this segment (Eq. ccd-error)       */
+    double ms;        /* minimum separation d >= 0 (Sec. 5.1)                */
+    double delta;     /* tolerance delta > 0                                 */
+    int64_t max_itr;  /* check limit m_I, 1 <= m_I <= the call's bound       */
+} ccd_segment;        /* 72 bytes, 8-byte aligned */
+
+/*
+ * Launch shapes of the solver kernels.  They change speed only: results are
+ * identical for every valid tuning.  A zero field takes the default.
+ *  deep_threads         threads of a deep-solver block, 256 or 512 (512)
+ *  deep_slots           deep-solver blocks / frontier slots (one per SM)
+ *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
+ *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
+ */
+typedef struct {
+    int32_t deep_threads;
+    int32_t deep_slots;
+    int32_t small_blocks_per_sm;
+    int32_t small_cap;
+} ccd_tuning;
+
+/* Workspace bytes for ccd_multi_batch (tuning may be NULL for defaults). */
+size_t ccd_multi_workspace_bytes(int64_t n, int64_t max_itr_bound, const ccd_tuning *tuning);
+
+/*
+ * One batch over all segments (both kinds), with one launch per solver
+ * stage.  segs: DEVICE array of nseg segments (read on the device, so a
+ * captured CUDA graph can be replayed with new segment contents);
+ * max_itr_bound: an upper bound on every segment's max_itr, used to size the
+ * deep frontier slots.  Outputs as for ccd_vf_batch, per query.  The
+ * segment table is checked on the device: a table that does not tile
+ * [0, n), or has a bad kind, delta <= 0, ms < 0, max_itr < 1 or max_itr >
+ * max_itr_bound, sets the workspace status to CCD_ERR_ARG and no query is
+ * answered.  Host-side errors as for ccd_vf_batch, plus CCD_ERR_ARG for
+ * nseg < 1 with n > 0, a NULL segs, or an invalid tuning.
+ */
+ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
+                           int64_t max_itr_bound, uint8_t *collides, double *toi,
+                           double *out_tol, int64_t *checks, const ccd_tuning *tuning,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Writes each segment's err[] from the bounds of its own points (Eq.
+ * ccd-error, or Eq. msccd-error when the segment's ms > 0; the constant
+ * follows the segment's kind), as ccd_err_from_bounds does for one scene.
+ * segs is a DEVICE array that this call updates in place.
+ */
+ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segment *segs,
+                                        int32_t nseg, void *stream);
+
+/*
  * Vertex-face batch that allocates nothing (the paper has no counterpart;
  * this is a deployment variant of ccd_vf_batch).
  *

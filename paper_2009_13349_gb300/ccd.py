@@ -11,6 +11,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -54,6 +55,14 @@ def lib():
         L.ccd_workspace_counters.restype = ctypes.c_int
         L.ccd_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
         L.ccd_set_stage_events.restype = ctypes.c_int
+        tp = ctypes.POINTER(Tuning)
+        L.ccd_multi_workspace_bytes.argtypes = [i64, i64, tp]
+        L.ccd_multi_workspace_bytes.restype = sz
+        L.ccd_multi_batch.argtypes = [dp, i64, vp, ctypes.c_int32, i64, vp, dp, dp, vp, tp, vp,
+                                      sz, vp]
+        L.ccd_multi_batch.restype = ctypes.c_int
+        L.ccd_segments_err_from_bounds.argtypes = [dp, i64, vp, ctypes.c_int32, vp]
+        L.ccd_segments_err_from_bounds.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
         L.ccd_status_str.restype = ctypes.c_char_p
         L.ccd_fp64_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -197,6 +206,100 @@ def fp64_peak_probe(blocks: int, iters: int, stream=None):
     _check(lib().ccd_fp64_peak_probe(int(blocks), int(iters), ctypes.byref(ms), _stream(stream)),
            "ccd_fp64_peak_probe")
     return ms.value, blocks * 256 * iters * 8
+
+
+# ---- multi-instance batches -------------------------------------------------------
+
+SEGMENT_DTYPE = np.dtype([("offset", "<i8"), ("count", "<i8"), ("kind", "<i4"),
+                          ("reserved", "<i4"), ("err", "<f8", (3,)), ("ms", "<f8"),
+                          ("delta", "<f8"), ("max_itr", "<i8")])
+assert SEGMENT_DTYPE.itemsize == 72
+
+
+class Tuning(ctypes.Structure):
+    """ccd_tuning: launch shapes only (results never depend on them)."""
+    _fields_ = [("deep_threads", ctypes.c_int32), ("deep_slots", ctypes.c_int32),
+                ("small_blocks_per_sm", ctypes.c_int32), ("small_cap", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _tuning_ptr(tuning):
+    if tuning is None:
+        return None
+    if isinstance(tuning, dict):
+        tuning = Tuning(**tuning)
+    return ctypes.pointer(tuning)
+
+
+def make_segments(counts, kinds, ms=0.0, delta=1e-6, max_itr=10**6, err=None) -> np.ndarray:
+    """Host segment table (structured array) tiling [0, sum(counts))."""
+    counts = np.asarray(counts, dtype=np.int64)
+    k = len(counts)
+    seg = np.zeros(k, dtype=SEGMENT_DTYPE)
+    seg["offset"] = np.concatenate([[0], np.cumsum(counts)[:-1]]) if k else []
+    seg["count"] = counts
+    seg["kind"] = np.broadcast_to(np.asarray(kinds, dtype=np.int32), (k,))
+    seg["ms"] = np.broadcast_to(np.asarray(ms, dtype=np.float64), (k,))
+    seg["delta"] = np.broadcast_to(np.asarray(delta, dtype=np.float64), (k,))
+    seg["max_itr"] = np.broadcast_to(np.asarray(max_itr, dtype=np.int64), (k,))
+    if err is not None:
+        seg["err"] = np.asarray(err, dtype=np.float64).reshape(k, 3)
+    return seg
+
+
+def segments_to_device(seg: np.ndarray, device=None) -> torch.Tensor:
+    """Copy a segment table to the device (as raw bytes)."""
+    raw = torch.from_numpy(np.ascontiguousarray(seg).view(np.uint8).copy())
+    return raw.to(device or "cuda")
+
+
+def segments_from_device(seg_dev: torch.Tensor) -> np.ndarray:
+    return seg_dev.cpu().numpy().view(SEGMENT_DTYPE).copy()
+
+
+def multi_workspace_bytes(n: int, max_itr_bound: int, tuning=None) -> int:
+    return int(lib().ccd_multi_workspace_bytes(int(n), int(max_itr_bound), _tuning_ptr(tuning)))
+
+
+def multi_workspace(n: int, max_itr_bound: int, tuning=None, device=None) -> torch.Tensor:
+    nbytes = multi_workspace_bytes(n, max_itr_bound, tuning)
+    if nbytes == 0:
+        raise CCDError(-1, "ccd_multi_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def segments_err_from_bounds(verts: torch.Tensor, seg_dev: torch.Tensor, stream=None) -> None:
+    _require_cuda(verts, "verts", torch.float64)
+    nseg = seg_dev.numel() // SEGMENT_DTYPE.itemsize
+    _check(lib().ccd_segments_err_from_bounds(_ptr(verts), verts.shape[1], _ptr(seg_dev), nseg,
+                                              _stream(stream)), "ccd_segments_err_from_bounds")
+
+
+def multi_batch(verts: torch.Tensor, seg_dev: torch.Tensor, max_itr_bound: int,
+                ws: torch.Tensor | None = None, out: Result | None = None, tuning=None,
+                with_checks: bool = True, stream=None) -> Result:
+    """ccd_multi_batch over every segment of the device table ``seg_dev``."""
+    _require_cuda(verts, "verts", torch.float64)
+    if verts.dim() != 2 or verts.shape[0] != 24:
+        raise ValueError("verts must have shape (24, n)")
+    n = verts.shape[1]
+    nseg = seg_dev.numel() // SEGMENT_DTYPE.itemsize
+    dev = verts.device
+    if out is None:
+        out = Result(torch.empty(n, dtype=torch.uint8, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.int64, device=dev) if with_checks else None)
+    if ws is None:
+        ws = multi_workspace(n, max_itr_bound, tuning, dev)
+    code = lib().ccd_multi_batch(_ptr(verts), n, _ptr(seg_dev), nseg, int(max_itr_bound),
+                                 _ptr(out.collides), _ptr(out.toi), _ptr(out.out_tol),
+                                 _ptr(out.checks), _tuning_ptr(tuning), _ptr(ws), ws.numel(),
+                                 _stream(stream))
+    _check(code, "ccd_multi_batch")
+    return out
 
 
 def to_soa(verts_aos, device="cuda") -> torch.Tensor:

@@ -447,6 +447,24 @@ struct Params {
     double *kappa;
 };
 
+// Per-query parameters of Algorithm 2: eps (Eq. ccd-error), ms, delta, m_I.
+struct QP {
+    double eps[3];
+    double ms, delta;
+    long long max_itr;
+};
+
+__device__ __forceinline__ QP qp_single(const Params &p, long long i)
+{
+    QP q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q.eps[c] = __ldg(p.err + (size_t)p.err_stride * i + c);
+    q.ms = p.ms;
+    q.delta = p.delta;
+    q.max_itr = p.max_itr;
+    return q;
+}
+
 __device__ __forceinline__ void write_result(const Params &p, long long qi, int c, double toi,
                                              double tol, long long n)
 {
@@ -459,15 +477,11 @@ __device__ __forceinline__ void write_result(const Params &p, long long qi, int 
 // ---- 1. level-0 filter ------------------------------------------------------
 
 template <int KIND>
-__global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
+__device__ __forceinline__ void root_query(const Params &p, long long i, const QP &q)
 {
-    const long long i = (long long)blockIdx.x * ROOT_THREADS + threadIdx.x;
-    if (i >= p.n) return;
     Query Q;
     load_query(p.verts, p.n, i, Q);
-    double eps[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) eps[c] = __ldg(p.err + (size_t)p.err_stride * i + c);
+    const double(&eps)[3] = q.eps;
 
     // Corners of [0,1]^3.  At t = 0 the position x0 + dx*0 equals x0 and at
     // t = 1 it is x0 + dx; with u, v in {0, 1} the products u e1, v e2 are
@@ -513,12 +527,12 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
         m[c] = lo;
         M[c] = hi;
     }
-    BoxTest bt = box_test(m, M, eps, p.ms, p.delta);
+    BoxTest bt = box_test(m, M, eps, q.ms, q.delta);
     if (!bt.hit) {
         write_result(p, i, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0, 1);
         return;
     }
-    if (1 >= p.max_itr || bt.term) {      // first colliding box of level 0
+    if (1 >= q.max_itr || bt.term) {      // first colliding box of level 0
         write_result(p, i, 1, 0.0, bt.w, 1);
         return;
     }
@@ -547,6 +561,14 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
     p.surv[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
+{
+    const long long i = (long long)blockIdx.x * ROOT_THREADS + threadIdx.x;
+    if (i >= p.n) return;
+    root_query<KIND>(p, i, qp_single(p, i));
+}
+
 // ---- 2./3. per-query level-synchronous solver --------------------------------
 
 // Runs Algorithm 2 for query qi with BS cooperating threads.  Returns false
@@ -566,8 +588,8 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 }
 
 template <int KIND, int BS>
-__device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, long long cap,
-                            bool fallback, Smem<BS> &s, double *tq)
+__device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur, Box *nxt,
+                            long long cap, bool fallback, Smem<BS> &s, double *tq)
 {
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
@@ -579,14 +601,11 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
         Q.x0[tid] = a;
         Q.dx[tid] = dsub(b, a);
     }
-    double eps[3], kap[3];
+    double kap[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        eps[c] = __ldg(p.err + (size_t)p.err_stride * qi + c);
-        kap[c] = p.kappa[3 * qi + c];
-    }
+    for (int c = 0; c < 3; ++c) kap[c] = p.kappa[3 * qi + c];
     Thresholds TH;
-    make_thresholds(eps, p.delta, TH);
+    make_thresholds(q.eps, q.delta, TH);
     constexpr int W = TWidth<KIND>::W;
     int k[3] = {0, 0, 0};
     long long size = 1;
@@ -634,12 +653,12 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 corners_keys<KIND>(tq + (2 * run) * W, tq + (2 * run + 1) * W,
                                    dyadic(b.a[1], k[1]), dyadic(b.a[1] + 1, k[1]),
                                    dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), km, kM);
-                box_test_keys(km, kM, TH, p.ms, bt.hit, bt.term, bt.w);
+                box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
             }
             evals += (unsigned long long)min((long long)BS, size - base);
             const long long nb = n_before + i + 1;
             const int fc = block_min<BS>(bt.hit ? tid : BIG, s);
-            const int cut = block_min<BS>((bt.hit && nb >= p.max_itr) ? tid : BIG, s);
+            const int cut = block_min<BS>((bt.hit && nb >= q.max_itr) ? tid : BIG, s);
             if (!found && fc != BIG) {
                 found = true;
                 if (tid == fc) {
@@ -653,7 +672,7 @@ __device__ bool solve_query(const Params &p, long long qi, Box *cur, Box *nxt, l
                 const bool term = s.first_term;
                 bsync<BS>();
                 const long long nfc = n_before + base + fc + 1;
-                if (nfc >= p.max_itr || term || !can_split) {
+                if (nfc >= q.max_itr || term || !can_split) {
                     if (tid == 0) {
                         write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
                         count_done(p, fallback, nfc, evals, tqs);
@@ -800,9 +819,149 @@ __global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slot
         __syncthreads();
         if (idx >= *(volatile const int *)count) return;
         const long long qi = list[idx];
-        const bool done = solve_query<KIND, BS>(p, qi, cur, nxt, cap, deep != 0, s, tq);
+        const bool done =
+            solve_query<KIND, BS>(p, qp_single(p, qi), qi, cur, nxt, cap, deep != 0, s, tq);
         if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
         __syncthreads();
+    }
+}
+
+// ---- multi-instance (segmented) kernels ---------------------------------------
+
+static_assert(sizeof(ccd_segment) == 72, "ccd_segment layout");
+
+// Segment of query i: the last segment whose offset is <= i.
+__device__ __forceinline__ int find_segment(const ccd_segment *segs, int nseg, long long i)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].offset <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
+{
+    QP q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q.eps[c] = sg.err[c];
+    q.ms = sg.ms;
+    q.delta = sg.delta;
+    q.max_itr = sg.max_itr;
+    return q;
+}
+
+__global__ void seg_validate_kernel(const ccd_segment *segs, int nseg, long long n,
+                                    long long max_itr_bound, Header *hdr)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const ccd_segment g = segs[s];
+    const long long start = s == 0 ? 0 : segs[s - 1].offset + segs[s - 1].count;
+    bool ok = g.offset == start && g.count >= 0 && (g.kind == CCD_KIND_VF || g.kind == CCD_KIND_EE) &&
+              g.delta > 0.0 && g.ms >= 0.0 && g.max_itr >= 1 && g.max_itr <= max_itr_bound;
+    if (s == nseg - 1) ok = ok && g.offset + g.count == n;
+    if (!ok) atomicExch(&hdr->status, (int)CCD_ERR_ARG);
+}
+
+__global__ void __launch_bounds__(ROOT_THREADS)
+    root_kernel_seg(Params p, const ccd_segment *segs, int nseg)
+{
+    if (*(volatile int *)&p.hdr->status == (int)CCD_ERR_ARG) return;
+    const long long i = (long long)blockIdx.x * ROOT_THREADS + threadIdx.x;
+    if (i >= p.n) return;
+    const ccd_segment sg = segs[find_segment(segs, nseg, i)];
+    const QP q = qp_segment(sg);
+    if (sg.kind == CCD_KIND_VF) root_query<CCD_KIND_VF>(p, i, q);
+    else root_query<CCD_KIND_EE>(p, i, q);
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS)
+    solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
+                     long long cap)
+{
+    __shared__ Smem<BS> s;
+    __shared__ int s_idx;
+    extern __shared__ double tq[];   // [2 * BS][TWidth<EE>::W]: sized for either kind
+    Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
+    Box *nxt = cur + cap;
+    const int *list = deep ? p.over : p.surv;
+    const int *count = deep ? &p.hdr->overflow : &p.hdr->survivors;
+    int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(head, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= *(volatile const int *)count) return;
+        const long long qi = list[idx];
+        const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
+        const QP q = qp_segment(sg);
+        const bool done =
+            sg.kind == CCD_KIND_VF
+                ? solve_query<CCD_KIND_VF, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq)
+                : solve_query<CCD_KIND_EE, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq);
+        if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
+        __syncthreads();
+    }
+}
+
+// per-segment eps from the segment's own points
+__global__ void seg_err_init_kernel(ccd_segment *segs, int nseg)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nseg)
+        for (int c = 0; c < 3; ++c) segs[s].err[c] = 1.0;
+}
+
+__global__ void seg_err_reduce_kernel(const double *__restrict__ verts, long long n,
+                                      ccd_segment *segs, int nseg)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        double mx[3] = {0.0, 0.0, 0.0};
+        int sid = -1;
+        if (valid) {
+            sid = find_segment(segs, nseg, i);
+#pragma unroll
+            for (int k = 0; k < 24; ++k)
+                mx[k % 3] = fmax(mx[k % 3], fabs(verts[(size_t)k * n + i]));
+        }
+        const int s0 = __shfl_sync(FULL, sid, 0);
+        const bool same = __all_sync(FULL, !valid || sid == s0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            unsigned long long *dst = (unsigned long long *)&segs[valid ? sid : 0].err[c];
+            if (same) {
+                double v = mx[c];
+                for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+                if (lane == 0 && s0 >= 0)
+                    atomicMax((unsigned long long *)&segs[s0].err[c],
+                              (unsigned long long)__double_as_longlong(v));
+            } else if (valid) {
+                atomicMax(dst, (unsigned long long)__double_as_longlong(mx[c]));
+            }
+        }
+    }
+}
+
+__global__ void seg_err_finish_kernel(ccd_segment *segs, int nseg)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const bool ms = segs[s].ms > 0.0;
+    const double K = segs[s].kind == CCD_KIND_VF ? (ms ? 7.549516567451064e-15 : 6.661338147750939e-15)
+                                                 : (ms ? 7.105427357601002e-15 : 6.217248937900877e-15);
+    for (int c = 0; c < 3; ++c) {
+        const double g = segs[s].err[c];
+        segs[s].err[c] = dmul(K, dmul(dmul(g, g), g));
     }
 }
 
@@ -1114,6 +1273,156 @@ ccd_status ccd_fp64_peak_probe(int blocks, int iters, float *ms_out, void *strea
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) r = CCD_ERR_CUDA;
     return r;
+}
+
+}  // extern "C"
+
+
+namespace {
+
+// ---- multi-instance host side ---------------------------------------------------
+
+struct Tuned {
+    int deep_threads, deep_slots, small_blocks_per_sm;
+    long long small_cap;
+};
+
+bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
+{
+    Tuned r{DEEP_THREADS, sms, SMALL_BLOCKS_PER_SM, SMALL_CAP};
+    if (t) {
+        if (t->deep_threads) r.deep_threads = t->deep_threads;
+        if (t->deep_slots) r.deep_slots = t->deep_slots;
+        if (t->small_blocks_per_sm) r.small_blocks_per_sm = t->small_blocks_per_sm;
+        if (t->small_cap) r.small_cap = t->small_cap;
+    }
+    if (r.deep_threads != 256 && r.deep_threads != 512) return false;
+    if (r.deep_slots < 1 || r.small_blocks_per_sm < 1 || r.small_blocks_per_sm > 32 ||
+        r.small_cap < 64)
+        return false;
+    *out = r;
+    return true;
+}
+
+size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
+{
+    size_t off = align256(sizeof(Header));
+    off = align256(off + sizeof(int) * (size_t)n);          // survivors
+    off = align256(off + sizeof(int) * (size_t)n);          // overflow
+    off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
+    off = align256(off + sizeof(Box) * 2 * (size_t)T.small_cap * (size_t)(sms * T.small_blocks_per_sm));
+    return off;
+}
+
+template <int DT>
+ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int nseg, char *ws,
+                                size_t off_small, int nb_small, long long cap_small,
+                                size_t off_deep, int nb_deep, long long cap_deep, cudaStream_t st)
+{
+    const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
+    const size_t tq_deep = sizeof(double) * 2 * DT * TWidth<CCD_KIND_EE>::W;
+    if (cudaFuncSetAttribute(solve_kernel_seg<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tq_deep) != cudaSuccess)
+        return CCD_ERR_CUDA;
+    solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
+        p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
+    stage_mark(2, st);
+    solve_kernel_seg<DT><<<nb_deep, DT, tq_deep, st>>>(p, segs, nseg, 1, (Box *)(ws + off_deep),
+                                                       cap_deep);
+    stage_mark(3, st);
+    return CCD_OK;
+}
+
+ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
+                     int64_t max_itr_bound, uint8_t *collides, double *toi, double *out_tol,
+                     int64_t *checks, const ccd_tuning *tuning, void *workspace, size_t ws_bytes,
+                     void *stream)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr_bound <= 0 || nseg < 0) return CCD_ERR_ARG;
+    if (n > 0 && (!verts || !segs || nseg < 1 || !collides || !toi || !out_tol)) return CCD_ERR_ARG;
+    if (!workspace) return CCD_ERR_WORKSPACE;
+    const int sms = device_sms();
+    if (sms <= 0) return CCD_ERR_CUDA;
+    Tuned T;
+    if (!resolve_tuning(tuning, sms, &T)) return CCD_ERR_ARG;
+    const size_t fixed = multi_fixed_bytes(n, sms, T);
+    const size_t per = sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound);
+    if (ws_bytes < fixed + per) return CCD_ERR_WORKSPACE;
+    long long nb_deep = (long long)((ws_bytes - fixed) / per);
+    if (nb_deep > T.deep_slots) nb_deep = T.deep_slots;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    if (cudaMemsetAsync(ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
+    if (n == 0) return CCD_OK;
+
+    Params p;
+    p.verts = verts; p.n = n; p.err = nullptr; p.err_stride = 0;
+    p.ms = 0.0; p.delta = 0.0; p.max_itr = 0;
+    p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
+    p.hdr = (Header *)ws;
+    size_t off = align256(sizeof(Header));
+    p.surv = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
+    const size_t off_small = off;
+    const int nb_small = sms * T.small_blocks_per_sm;
+
+    seg_validate_kernel<<<(nseg + 255) / 256, 256, 0, st>>>(segs, nseg, n, max_itr_bound, p.hdr);
+    stage_mark(0, st);
+    root_kernel_seg<<<(unsigned)((n + ROOT_THREADS - 1) / ROOT_THREADS), ROOT_THREADS, 0, st>>>(
+        p, segs, nseg);
+    stage_mark(1, st);
+    ccd_status r = T.deep_threads == 256
+                       ? launch_multi_solvers<256>(p, segs, nseg, ws, off_small, nb_small,
+                                                   T.small_cap, fixed, (int)nb_deep,
+                                                   deep_cap(max_itr_bound), st)
+                       : launch_multi_solvers<512>(p, segs, nseg, ws, off_small, nb_small,
+                                                   T.small_cap, fixed, (int)nb_deep,
+                                                   deep_cap(max_itr_bound), st);
+    if (r != CCD_OK) return r;
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ccd_multi_workspace_bytes(int64_t n, int64_t max_itr_bound, const ccd_tuning *tuning)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr_bound <= 0) return 0;
+    const int sms = device_sms();
+    if (sms <= 0) return 0;
+    Tuned T;
+    if (!resolve_tuning(tuning, sms, &T)) return 0;
+    return multi_fixed_bytes(n, sms, T) +
+           sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound) * (size_t)T.deep_slots;
+}
+
+ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
+                           int64_t max_itr_bound, uint8_t *collides, double *toi,
+                           double *out_tol, int64_t *checks, const ccd_tuning *tuning,
+                           void *workspace, size_t ws_bytes, void *stream)
+{
+    return run_multi(verts, n, segs, nseg, max_itr_bound, collides, toi, out_tol, checks, tuning,
+                     workspace, ws_bytes, stream);
+}
+
+ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segment *segs,
+                                        int32_t nseg, void *stream)
+{
+    if (n < 0 || n >= 0x7fffffffLL || nseg < 1 || !segs || (n > 0 && !verts)) return CCD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned sb = (unsigned)((nseg + 255) / 256);
+    seg_err_init_kernel<<<sb, 256, 0, st>>>(segs, nseg);
+    if (n > 0) {
+        const int sms = device_sms();
+        long long blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms) blocks = 8LL * sms;
+        seg_err_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, n, segs, nseg);
+    }
+    seg_err_finish_kernel<<<sb, 256, 0, st>>>(segs, nseg);
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
 
 }  // extern "C"
