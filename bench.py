@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deep-slots", type=int, default=None,
                     help="cap the deep-solver slots (smaller workspace, e.g. for profiling)")
+    ap.add_argument("--workload", default="simulation-mixed",
+                    choices=["simulation-mixed", "multi-instance", "served"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="multi-instance/served: fraction of the full query count")
+    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of arrivals")
+    ap.add_argument("--req-scale", type=float, default=0.1,
+                    help="served: request sizes are log-uniform in [100, 500k] times this")
+    ap.add_argument("--retune", action="store_true")
     return ap.parse_args()
 
 
@@ -354,10 +362,224 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def _gpu_name(torch, dev):
+    return torch.cuda.get_device_properties(dev).name
+
+
+def run_multi_instance(args):
+    """64 simulation instances (log-uniform sizes, ~20M queries, VF:EE 1:1,
+    per-instance scale and eps): the plain form (one err + batch call per
+    instance-kind, in sequence) against the batched form (one multi-instance
+    call for all, replayed from a CUDA graph, autotuned launch shapes)."""
+    import torch
+    from paper_2009_13349_gb300 import autotune, ccd
+    from paper_2009_13349_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    wl = W.multi_instance(count=64, total=int(20_000_000 * args.scale), seed=3)
+    counts = [b.n for b in wl.batches]
+    kinds = [b.kind for b in wl.batches]
+    n = sum(counts)
+    verts = torch.empty((24, n), dtype=torch.float64, device=dev)
+    parts, off = [], 0
+    for b in wl.batches:
+        t = ccd.to_soa(b.verts, dev)
+        verts[:, off:off + b.n].copy_(t)
+        parts.append(t)
+        off += b.n
+    seg = ccd.make_segments(counts, kinds, 0.0, 1e-6, 10**6)
+    sd = ccd.segments_to_device(seg, dev)
+    s = torch.cuda.Stream(dev)
+
+    # autotune on a sample: the first instances up to ~2M queries
+    k, acc = 0, 0
+    while k < len(counts) and acc < 2_000_000:
+        acc += counts[k]
+        k += 1
+    sv = verts[:, :acc].contiguous()
+    ssd = ccd.segments_to_device(seg[:k], dev)
+    ccd.segments_err_from_bounds(sv, ssd)
+
+    def measure(t):
+        ws = ccd.multi_workspace(acc, 10**6, t, dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ccd.multi_batch(sv, ssd, 10**6, ws=ws, tuning=t, with_checks=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    tuning, timings = autotune.get_or_tune(_gpu_name(torch, dev), "multi-instance", measure,
+                                           autotune.candidates(sms), reps=1, retune=args.retune)
+    del sv, ssd
+
+    out = ccd.Result(torch.empty(n, dtype=torch.uint8, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev), None)
+    ws = ccd.multi_workspace(n, 10**6, tuning, dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        ccd.segments_err_from_bounds(verts, sd, stream=s)
+        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ccd.segments_err_from_bounds(verts, sd, stream=s)
+        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = Clocks(0)
+    clocks.start()
+    ev[0].record(s)
+    for i in range(args.steps):
+        with torch.cuda.stream(s):
+            g.replay()
+        ev[i + 1].record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    batched_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    batched = (out.collides.cpu().numpy(), out.toi.cpu().numpy(), out.out_tol.cpu().numpy())
+
+    # plain form: one call per instance-kind, in sequence on one stream
+    wsp = ccd.workspace(max(counts), 10**6, dev)
+    plain_out = [None] * len(parts)
+
+    def plain_step():
+        for j, (t, kind) in enumerate(zip(parts, kinds)):
+            e = ccd.err_from_bounds(kind, t)
+            plain_out[j] = ccd.batch(kind, t, e, delta=1e-6, max_itr=10**6, ws=wsp,
+                                     out=plain_out[j], with_checks=False)
+
+    for _ in range(max(1, args.warmup)):
+        plain_step()
+    torch.cuda.synchronize()
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    pev[0].record()
+    for i in range(args.steps):
+        plain_step()
+        pev[i + 1].record()
+    torch.cuda.synchronize()
+    plain_ms = [pev[i].elapsed_time(pev[i + 1]) for i in range(args.steps)]
+    same = True
+    off = 0
+    for j, c in enumerate(counts):
+        r = plain_out[j]
+        same &= bool(np.array_equal(r.collides.cpu().numpy(), batched[0][off:off + c]))
+        same &= bool(np.array_equal(r.toi.cpu().numpy(), batched[1][off:off + c]))
+        same &= bool(np.array_equal(r.out_tol.cpu().numpy(), batched[2][off:off + c]))
+        off += c
+    fn = 0
+    off = 0
+    for b in wl.batches:
+        hit = b.truth == 1
+        fn += int(np.sum(batched[0][off:off + b.n][hit] == 0))
+        off += b.n
+    bm, pm = float(np.mean(batched_ms)), float(np.mean(plain_ms))
+    print(json.dumps({
+        "metric": METRIC, "value": n / (bm * 1e-3), "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"multi-instance: 64 instances, {n} queries (VF:EE 1:1), seed 3",
+                   "delta": 1e-6, "max_itr": 10**6, "form": "batched, CUDA graph replay",
+                   "tuning": tuning},
+        "plain": {"value": n / (pm * 1e-3), "ms_per_step": pm,
+                  "form": "one err + batch call per instance-kind (128 calls)"},
+        "speedup_vs_plain": pm / bm,
+        "latency_ms": {"p50": float(np.percentile(batched_ms, 50)),
+                       "p99": float(np.percentile(batched_ms, 99)),
+                       "plain_p50": float(np.percentile(plain_ms, 50)),
+                       "plain_p99": float(np.percentile(plain_ms, 99))},
+        "identical_to_plain": same, "false_negatives": fn, "clocks": clk,
+        "autotune": None if timings is None else [[t, s_] for t, s_ in timings],
+    }))
+
+
+def run_served(args):
+    """16 clients with Poisson arrivals; request sizes log-uniform in
+    [100, 500k] x --req-scale (uniform unit-cube generator), delta in
+    {1e-4, 1e-6}, ms in {0, 1e-4}, m_I = 1e6; continuous batching on 4 lanes
+    within 40 GB against one call per request, at offered loads 0.7 and 1.2
+    of the capacity measured on the same request mix."""
+    import torch
+    from paper_2009_13349_gb300 import workloads as W
+    from paper_2009_13349_gb300.serve import (GpuExecutor, Request, Server, latency_stats,
+                                              run_stream, serial_baseline)
+    dev = torch.device("cuda", 0)
+    lo = max(1, int(round(100 * args.req_scale)))
+    hi = max(lo + 1, int(round(500_000 * args.req_scale)))
+    pool_n = max(4 * hi, 100_000)
+    pools = {k: torch.from_numpy(W.unit_cube(k, pool_n, seed=40 + k).verts).pin_memory()
+             for k in (0, 1)}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    tuning = {"deep_threads": 512, "deep_slots": max(8, sms // 4), "small_blocks_per_sm": 16,
+              "small_cap": 1024}
+    lanes = 4
+    ex = GpuExecutor(lanes, 10**6, tuning, dev)
+    rng = np.random.default_rng(4)
+
+    def draw(i, t):
+        size = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        kind = int(rng.integers(0, 2))
+        a = int(rng.integers(0, pool_n - size))
+        return Request(i, kind, pools[kind][a:a + size], delta=float(rng.choice([1e-4, 1e-6])),
+                       ms=float(rng.choice([0.0, 1e-4])), max_itr=10**6, arrival=t)
+
+    # capacity on the request mix: 32 requests in one batch, after a warm-up
+    mix = [draw(i, 0.0) for i in range(32)]
+    h = ex.launch(0, mix[:4])
+    ex.harvest(h, mix[:4])
+    t0 = time.perf_counter()
+    h = ex.launch(0, mix)
+    ex.harvest(h, mix)
+    cap = sum(r.n for r in mix) / (time.perf_counter() - t0)
+    mean_size = (hi - lo) / np.log(hi / lo)
+    results = {}
+    for load in (0.7, 1.2):
+        rate = load * cap / mean_size / 16.0
+        spec = []
+        for c in range(16):
+            t = 0.0
+            while True:
+                t += rng.exponential(1.0 / rate)
+                if t > args.duration:
+                    break
+                spec.append(t)
+        spec.sort()
+        state = rng.bit_generator.state
+        reqs_a = [draw(i, t) for i, t in enumerate(spec)]
+        rng.bit_generator.state = state
+        reqs_b = [draw(i, t) for i, t in enumerate(spec)]
+        srv = Server(ex, lanes=lanes, budget=40 << 30, max_batch=1_000_000)
+        run_stream(srv, reqs_a)
+        serial_baseline(GpuExecutor(1, 10**6, tuning, dev), reqs_b)
+        same = all(np.array_equal(a.collides, b.collides) and np.array_equal(a.toi, b.toi)
+                   and np.array_equal(a.out_tol, b.out_tol) for a, b in zip(reqs_a, reqs_b))
+        results[str(load)] = {"served": latency_stats(reqs_a),
+                              "one_call_per_request": latency_stats(reqs_b),
+                              "identical": bool(same), "requests": len(spec),
+                              "peak_budget_bytes": srv.peak_bytes,
+                              "batches": srv._next_batch}
+    hi_load = results["1.2"]
+    print(json.dumps({
+        "metric": METRIC, "value": hi_load["served"]["queries_per_s"], "unit": "queries/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"served: 16 Poisson clients, sizes log-uniform {lo}..{hi} "
+                               "(unit-cube generator), delta {1e-4,1e-6}, ms {0,1e-4}, m_I 1e6, "
+                               "40 GB budget, 4 lanes",
+                   "duration_s": args.duration, "capacity_queries_per_s": cap,
+                   "tuning": tuning},
+        "loads": results}))
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "multi-instance":
+        run_multi_instance(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_native(args)
 

@@ -216,6 +216,14 @@ ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segm
                                         int32_t nseg, void *stream);
 
 /*
+ * Layout helper: copies n queries from an array of structures aos[n][24]
+ * (query-major, the same 24-value order) into columns [0, n) of a structure
+ * of arrays with plane stride ld >= n: soa[k * ld + i] = aos[i * 24 + k].
+ * Device pointers; soa may point into a larger batch array (column offset).
+ */
+ccd_status ccd_aos_to_soa(const double *aos, int64_t n, double *soa, int64_t ld, void *stream);
+
+/*
  * Vertex-face batch that allocates nothing (the paper has no counterpart;
  * this is a deployment variant of ccd_vf_batch).
  *

@@ -63,6 +63,8 @@ def lib():
         L.ccd_multi_batch.restype = ctypes.c_int
         L.ccd_segments_err_from_bounds.argtypes = [dp, i64, vp, ctypes.c_int32, vp]
         L.ccd_segments_err_from_bounds.restype = ctypes.c_int
+        L.ccd_aos_to_soa.argtypes = [dp, i64, dp, i64, vp]
+        L.ccd_aos_to_soa.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
         L.ccd_status_str.restype = ctypes.c_char_p
         L.ccd_fp64_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -300,6 +302,18 @@ def multi_batch(verts: torch.Tensor, seg_dev: torch.Tensor, max_itr_bound: int,
                                  _stream(stream))
     _check(code, "ccd_multi_batch")
     return out
+
+
+def aos_to_soa(aos: torch.Tensor, soa: torch.Tensor, col: int = 0, stream=None) -> None:
+    """Device (n, 24) array of structures into columns [col, col + n) of a
+    (24, ld) structure-of-arrays tensor (ccd_aos_to_soa)."""
+    _require_cuda(aos, "aos", torch.float64)
+    _require_cuda(soa, "soa", torch.float64)
+    n, ld = aos.shape[0], soa.shape[1]
+    if aos.dim() != 2 or aos.shape[1] != 24 or soa.shape[0] != 24 or col < 0 or col + n > ld:
+        raise ValueError("shape mismatch")
+    ptr = ctypes.c_void_p(soa.data_ptr() + 8 * col)
+    _check(lib().ccd_aos_to_soa(_ptr(aos), n, ptr, ld, _stream(stream)), "ccd_aos_to_soa")
 
 
 def to_soa(verts_aos, device="cuda") -> torch.Tensor:

@@ -965,6 +965,25 @@ __global__ void seg_err_finish_kernel(ccd_segment *segs, int nseg)
     }
 }
 
+// ---- layout helper: array of structures -> structure of arrays ---------------
+
+// Block of 256 queries: coalesced load of 256 x 24 doubles into shared
+// memory, then 24 coalesced plane writes.
+__global__ void __launch_bounds__(256) aos_to_soa_kernel(const double *__restrict__ aos,
+                                                         long long n, double *soa, long long ld)
+{
+    __shared__ double tile[256 * 25];   // padded rows against bank conflicts
+    const long long q0 = (long long)blockIdx.x * 256;
+    const int m = (int)min(256LL, n - q0);
+    for (int e = threadIdx.x; e < m * 24; e += 256) {
+        const int qi = e / 24, k = e - qi * 24;
+        tile[qi * 25 + k] = aos[(q0 + qi) * 24 + k];
+    }
+    __syncthreads();
+    if (threadIdx.x < m)
+        for (int k = 0; k < 24; ++k) soa[(size_t)k * ld + q0 + threadIdx.x] = tile[threadIdx.x * 25 + k];
+}
+
 // ---- eps from bounds (Eq. ccd-error / msccd-error) ---------------------------
 
 __global__ void err_init_kernel(unsigned long long *g)
@@ -1406,6 +1425,14 @@ ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *se
 {
     return run_multi(verts, n, segs, nseg, max_itr_bound, collides, toi, out_tol, checks, tuning,
                      workspace, ws_bytes, stream);
+}
+
+ccd_status ccd_aos_to_soa(const double *aos, int64_t n, double *soa, int64_t ld, void *stream)
+{
+    if (n < 0 || ld < n || (n > 0 && (!aos || !soa))) return CCD_ERR_ARG;
+    if (n == 0) return CCD_OK;
+    aos_to_soa_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(aos, n, soa, ld);
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
 
 ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segment *segs,
