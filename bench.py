@@ -513,8 +513,11 @@ def run_served(args):
     pools = {k: torch.from_numpy(W.unit_cube(k, pool_n, seed=40 + k).verts).pin_memory()
              for k in (0, 1)}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    tuning = {"deep_threads": 512, "deep_slots": max(8, sms // 4), "small_blocks_per_sm": 16,
+    # every lane gets one deep slot per SM (a deep block fills an SM, so lanes
+    # take turns on the SMs); the 40 GB budget bounds the batches in flight
+    tuning = {"deep_threads": 512, "deep_slots": sms, "small_blocks_per_sm": 16,
               "small_cap": 1024}
+    serial_tuning = dict(tuning, deep_slots=sms)   # one request at a time: the whole GPU
     lanes = 4
     ex = GpuExecutor(lanes, 10**6, tuning, dev)
     rng = np.random.default_rng(4)
@@ -553,7 +556,7 @@ def run_served(args):
         reqs_b = [draw(i, t) for i, t in enumerate(spec)]
         srv = Server(ex, lanes=lanes, budget=40 << 30, max_batch=1_000_000)
         run_stream(srv, reqs_a)
-        serial_baseline(GpuExecutor(1, 10**6, tuning, dev), reqs_b)
+        serial_baseline(GpuExecutor(1, 10**6, serial_tuning, dev), reqs_b)
         same = all(np.array_equal(a.collides, b.collides) and np.array_equal(a.toi, b.toi)
                    and np.array_equal(a.out_tol, b.out_tol) for a, b in zip(reqs_a, reqs_b))
         results[str(load)] = {"served": latency_stats(reqs_a),

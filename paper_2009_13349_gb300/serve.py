@@ -64,11 +64,21 @@ class _Batch:
     handle: object = None
 
 
+def cost_class(r: Request) -> int:
+    """Requests whose minimum separation exceeds their tolerance subdivide a
+    whole |F| <= d region down to w(B) < delta (often to the check limit);
+    they are batched only with each other so that cheap requests do not wait
+    for them."""
+    return int(r.ms > 0.0 and r.delta < r.ms)
+
+
 class Server:
-    """Continuous batching over ``lanes`` executor lanes within ``budget`` bytes."""
+    """Continuous batching over ``lanes`` executor lanes within ``budget`` bytes.
+    A batch takes requests from the FIFO head while they share the head's
+    cost class (``classify``; None puts every request in one class)."""
 
     def __init__(self, executor, lanes: int = 4, budget: int = 40 << 30,
-                 max_batch: int = 1 << 20, clock=time.perf_counter):
+                 max_batch: int = 1 << 20, clock=time.perf_counter, classify=cost_class):
         self.ex = executor
         self.lanes = lanes
         self.budget = int(budget)
@@ -80,6 +90,7 @@ class Server:
         self.completed = []
         self._next_batch = 0
         self.peak_bytes = 0
+        self.classify = classify
 
     def batch_bytes(self, n: int) -> int:
         return int(n) * QUERY_BYTES + self.ex.workspace_bytes(int(n))
@@ -96,9 +107,12 @@ class Server:
         """Form one batch for a free lane from the FIFO head, within budget."""
         take, n = [], 0
         room = self.budget - self.in_flight_bytes
+        cls = self.classify(self.waiting[0]) if (self.classify and self.waiting) else None
         while self.waiting:
             r = self.waiting[0]
             if n + r.n > self.max_batch or self.batch_bytes(n + r.n) > room:
+                break
+            if cls is not None and self.classify(r) != cls:
                 break
             take.append(self.waiting.popleft())
             n += r.n

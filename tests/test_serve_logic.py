@@ -42,8 +42,8 @@ class FakeExecutor:
             r.out_tol = np.zeros(r.n)
 
 
-def req(i, n, kind=0):
-    return Request(i, kind, np.zeros((n, 24)))
+def req(i, n, kind=0, ms=0.0, delta=1e-6):
+    return Request(i, kind, np.zeros((n, 24)), ms=ms, delta=delta)
 
 
 def test_fifo_batching_and_routing():
@@ -118,3 +118,22 @@ def test_oversized_requests_are_rejected():
     s2 = Server(ex, lanes=1, budget=2000, max_batch=10**6, clock=clk)
     with pytest.raises(RejectedRequest):
         s2.submit(req(2, 10))
+
+
+def test_batches_keep_cost_classes_apart():
+    clk = FakeClock()
+    ex = FakeExecutor(clk)
+    s = Server(ex, lanes=3, budget=10**12, max_batch=1000, clock=clk)
+    s.submit(req(0, 10))
+    s.submit(req(1, 10))
+    s.submit(req(2, 10, ms=1e-4, delta=1e-6))     # separation above tolerance
+    s.submit(req(3, 10, ms=1e-4, delta=1e-6))
+    s.submit(req(4, 10, ms=1e-4, delta=1e-3))     # separation below tolerance: cheap
+    s.poll()
+    assert [h["reqs"] for h in ex.launches] == [[0, 1], [2, 3], [4]]
+    s2 = Server(FakeExecutor(clk), lanes=1, budget=10**12, max_batch=1000, clock=clk,
+                classify=None)
+    for i in range(5):
+        s2.submit(req(i, 10, ms=1e-4 * (i % 2)))
+    s2.poll()
+    assert [h["reqs"] for h in s2.ex.launches] == [[0, 1, 2, 3, 4]]
