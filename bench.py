@@ -63,10 +63,8 @@ def parse():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2009_13349_gb300 import parallel
+    return parallel.env()
 
 
 class Clocks:
@@ -116,6 +114,23 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def recorded_traffic(batches):
+    """DRAM bytes per deep-solver launch (mean over the kinds in the step)
+    from the committed ncu record, or None if the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "deep_solver.traffic.json")
+    src = os.path.join(ROOT, "paper_2009_13349_gb300", "csrc", "ccd.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    if rec.get("sha256_prefix") != sha:
+        return None
+    per = [rec["dram_bytes_per_launch"]["VF" if b.kind == 0 else "EE"] for b in batches]
+    return float(sum(per) / len(per))
 
 
 def make_workload(n, seed):
@@ -199,7 +214,8 @@ def run_native(args):
     dev = torch.device("cuda", local)
     from paper_2009_13349_gb300 import ccd
 
-    wl = make_workload(args.n, args.seed + rank)   # each rank its own batch (weak scaling)
+    from paper_2009_13349_gb300 import parallel
+    wl = make_workload(args.n, parallel.rank_seed(args.seed, rank))   # weak scaling
     batches = wl.batches
     verts = [ccd.to_soa(b.verts, dev) for b in batches]
     host = [torch.from_numpy(np.ascontiguousarray(b.verts.T)).pin_memory() for b in batches]
@@ -252,10 +268,7 @@ def run_native(args):
         dist.barrier()
     step_ms = [marks[s].elapsed_time(marks[s + 1]) for s in range(args.steps)]
     total_ms = marks[0].elapsed_time(marks[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = parallel.max_over_ranks(total_ms, device=dev)
     stage_ms = np.zeros((len(batches), 3))
     for s in range(args.steps):
         for j in range(len(batches)):
@@ -276,7 +289,7 @@ def run_native(args):
     checks = np.concatenate(checks)
 
     # roofline of the dominant kernel
-    names = ["root_kernel", "solve_kernel<32> (small frontier)", "solve_kernel<512> (deep)"]
+    names = ["root_kernel", "solve_kernel<32> (small frontier)", "solve_kernel<256> (deep)"]
     per_kernel = stage_ms.sum(axis=0)
     top = int(np.argmax(per_kernel))
     # executed FP64 arithmetic, from the kernel's own counters
@@ -290,8 +303,11 @@ def run_native(args):
         naive = sum(counters[j]["checks_" + sfx] * OPS_PER_CHECK[b.kind]
                     for j, b in enumerate(batches))
     achieved = alg_ops / (per_kernel[top] * 1e-3)
+    traffic = None
+    if names[top].startswith("solve_kernel<256>"):
+        traffic = recorded_traffic(batches)
     total_queries = sum(b.n for b in batches) * world
-    value = total_queries / (total_ms / args.steps * 1e-3)
+    value = parallel.job_throughput(sum(b.n for b in batches), world, total_ms / args.steps)
 
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
@@ -306,7 +322,7 @@ def run_native(args):
                        "p99": float(np.percentile(step_ms, 99))},
         "roofline": {"bound": "alu", "kernel": names[top], "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "GFLOP/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": traffic,
                      "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
                                     "(one FP64 pipe op = one add or mul; -fmad=false)",
                      "work": "executed FP64 add/sub/mul from the kernel's counters",
@@ -513,11 +529,11 @@ def run_served(args):
     pools = {k: torch.from_numpy(W.unit_cube(k, pool_n, seed=40 + k).verts).pin_memory()
              for k in (0, 1)}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    # every lane gets one deep slot per SM (a deep block fills an SM, so lanes
-    # take turns on the SMs); the 40 GB budget bounds the batches in flight
-    tuning = {"deep_threads": 512, "deep_slots": sms, "small_blocks_per_sm": 16,
+    # every lane gets the default deep slots (deep blocks fill the SMs, so
+    # lanes take turns); the 40 GB budget bounds the batches in flight
+    tuning = {"deep_threads": 256, "deep_slots": 2 * sms, "small_blocks_per_sm": 16,
               "small_cap": 1024}
-    serial_tuning = dict(tuning, deep_slots=sms)   # one request at a time: the whole GPU
+    serial_tuning = dict(tuning)   # one request at a time: the whole GPU
     lanes = 4
     ex = GpuExecutor(lanes, 10**6, tuning, dev)
     rng = np.random.default_rng(4)

@@ -50,7 +50,7 @@ typedef enum {
 
 /*
  * Bytes of device workspace that ccd_vf_batch / ccd_ee_batch need for n
- * queries at check limit max_itr with the default number of deep slots (one
+ * queries at check limit max_itr with the default number of deep slots (two
  * per SM of the current device).  One deep slot takes 48 * (2 * max_itr + 64)
  * bytes.  A smaller workspace is accepted as long as it holds at least one
  * deep slot; fewer slots only reduce parallelism on queries with very large
@@ -174,8 +174,8 @@ typedef struct {
 /*
  * Launch shapes of the solver kernels.  They change speed only: results are
  * identical for every valid tuning.  A zero field takes the default.
- *  deep_threads         threads of a deep-solver block, 256 or 512 (512)
- *  deep_slots           deep-solver blocks / frontier slots (one per SM)
+ *  deep_threads         threads of a deep-solver block, 256 or 512 (256)
+ *  deep_slots           deep-solver blocks / frontier slots (two per SM)
  *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
  *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
  */

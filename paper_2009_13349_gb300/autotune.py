@@ -26,7 +26,7 @@ FIELDS = ("deep_threads", "deep_slots", "small_blocks_per_sm", "small_cap")
 
 def candidates(sms: int) -> list[dict]:
     out = []
-    for dt, slots in ((512, sms), (256, sms), (256, 2 * sms)):
+    for dt, slots in ((256, 2 * sms), (512, sms), (256, sms)):
         for sb in (8, 16):
             for cap in (256, 1024):
                 out.append({"deep_threads": dt, "deep_slots": slots,

@@ -46,7 +46,8 @@ constexpr int ROOT_THREADS = 256;
 constexpr int SMALL_THREADS = 32;     // one warp per query
 constexpr int SMALL_BLOCKS_PER_SM = 16;
 constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
-constexpr int DEEP_THREADS = 512;
+constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
+constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM
 constexpr int BIG = 0x7fffffff;
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
@@ -1084,7 +1085,7 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
     const size_t per = sizeof(Box) * 2 * (size_t)want;
     long long nb = (long long)(room / per);
     if (nb >= 1) {
-        L.nb_deep = (int)(nb < sms ? nb : sms);
+        L.nb_deep = (int)(nb < (long long)DEEP_BLOCKS_PER_SM * sms ? nb : (long long)DEEP_BLOCKS_PER_SM * sms);
         L.cap_deep = want;
     } else {
         L.nb_deep = 1;
@@ -1163,7 +1164,8 @@ size_t ccd_workspace_bytes(int64_t n, int64_t max_itr)
     const int sms = device_sms();
     if (sms <= 0) return 0;
     Layout L = layout_fixed(n, sms);
-    return L.off_deep + sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)sms;
+    return L.off_deep +
+           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM * sms);
 }
 
 ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err, int err_stride,
@@ -1308,7 +1310,7 @@ struct Tuned {
 
 bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
 {
-    Tuned r{DEEP_THREADS, sms, SMALL_BLOCKS_PER_SM, SMALL_CAP};
+    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, SMALL_CAP};
     if (t) {
         if (t->deep_threads) r.deep_threads = t->deep_threads;
         if (t->deep_slots) r.deep_slots = t->deep_slots;
