@@ -76,6 +76,17 @@ def _lib():
                                              ctypes.c_longlong, ctypes.c_int, up, dp, dp,
                                              lp, ctypes.c_int]
             lib.oracle_ccd_batch.restype = ctypes.c_longlong
+            lib.oracle_ccd_t.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_longlong, ctypes.c_double,
+                                         ctypes.c_int, dp, dp, lp]
+            lib.oracle_ccd_t.restype = ctypes.c_int
+            lib.oracle_ccd_batch_t.argtypes = [ctypes.c_int, dp, ctypes.c_longlong, dp,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_longlong, ctypes.c_double, ctypes.c_int,
+                                               up, dp, dp, lp, ctypes.c_int]
+            lib.oracle_ccd_batch_t.restype = ctypes.c_longlong
+            lib.oracle_kappa_t.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
+            lib.oracle_kappa_t.restype = None
             _LIB = lib
         return _LIB
 
@@ -109,11 +120,11 @@ def box(kind: int, query, interval) -> tuple[np.ndarray, np.ndarray]:
     return m, M
 
 
-def kappa(kind: int, query) -> np.ndarray:
-    """(kappa_t, kappa_u, kappa_v) of Eq. (kappas)."""
+def kappa(kind: int, query, t_max: float = 1.0) -> np.ndarray:
+    """(kappa_t, kappa_u, kappa_v) of Eq. (kappas) over [0, t_max] x [0,1]^2."""
     q = _as_queries(query)[0]
     out = np.zeros(3)
-    _lib().oracle_kappa(kind, _dptr(q), _dptr(out))
+    _lib().oracle_kappa_t(kind, _dptr(q), float(t_max), _dptr(out))
     return out
 
 
@@ -133,22 +144,22 @@ def err_from_bounds(kind: int, verts, ms_nonzero: bool = False,
 
 
 def ccd(kind: int, query, err, ms: float = 0.0, delta: float = 1e-6,
-        max_itr: int = 10**6, flags: int = 0):
-    """One query -> (collides, toi, out_tol, checks)."""
+        max_itr: int = 10**6, flags: int = 0, t_max: float = 1.0):
+    """One query -> (collides, toi, out_tol, checks); time interval [0, t_max]."""
     q = _as_queries(query)[0]
     e = np.ascontiguousarray(np.asarray(err, dtype=np.float64).reshape(3))
     toi, tol = ctypes.c_double(), ctypes.c_double()
     n = ctypes.c_longlong()
-    r = _lib().oracle_ccd(kind, _dptr(q), _dptr(e), float(ms), float(delta),
-                          int(max_itr), int(flags), ctypes.byref(toi),
-                          ctypes.byref(tol), ctypes.byref(n))
+    r = _lib().oracle_ccd_t(kind, _dptr(q), _dptr(e), float(ms), float(delta),
+                            int(max_itr), float(t_max), int(flags), ctypes.byref(toi),
+                            ctypes.byref(tol), ctypes.byref(n))
     if r < 0:
         raise MemoryError("oracle queue allocation failed")
     return bool(r), toi.value, tol.value, n.value
 
 
 def ccd_batch(kind: int, verts, err, ms: float = 0.0, delta: float = 1e-6,
-              max_itr: int = 10**6, flags: int = 0, nthreads: int = 1):
+              max_itr: int = 10**6, flags: int = 0, nthreads: int = 1, t_max: float = 1.0):
     """n queries (n x 24) -> (collides u8, toi f64, out_tol f64, checks i64)."""
     v = _as_queries(verts)
     n = v.shape[0]
@@ -163,9 +174,9 @@ def ccd_batch(kind: int, verts, err, ms: float = 0.0, delta: float = 1e-6,
     toi = np.zeros(n)
     tol = np.zeros(n)
     chk = np.zeros(n, dtype=np.int64)
-    fails = _lib().oracle_ccd_batch(
+    fails = _lib().oracle_ccd_batch_t(
         kind, _dptr(v), n, _dptr(e), stride, float(ms), float(delta), int(max_itr),
-        int(flags), col.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _dptr(toi),
+        float(t_max), int(flags), col.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _dptr(toi),
         _dptr(tol), chk.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), int(nthreads))
     if fails:
         raise MemoryError(f"oracle queue allocation failed for {fails} queries")

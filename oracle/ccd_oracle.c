@@ -28,6 +28,10 @@
  *  - A split whose dimension already has width 2^-53 is not made: the query
  *    returns as at the check limit (keeps every endpoint an exact double).
  *  - F is evaluated with the fixed expression in corner_F below.
+ *  - SolveMSCCD's shortened time interval [0, t_max] (Sec. 6, line search)
+ *    is solved in s in [0,1]^3 with t = t_max * s rounded once: interval
+ *    endpoints stay exact dyadics in s, and kappa_t is taken over the
+ *    corners t = 0 and t = t_max.  t_max = 1 is the plain solver.
  */
 #include <math.h>
 #include <stdint.h>
@@ -73,16 +77,17 @@ void oracle_corner(int kind, const double *q, double t, double u, double v,
     }
 }
 
-/* Eq. (box): B_F(I) is the axis-aligned box of F at the 8 corners of I. */
-void oracle_box(int kind, const double *q, const double I[6], double m[3],
-                double M[3])
+/* Eq. (box): B_F(I) is the axis-aligned box of F at the 8 corners of I;
+ * I[0..1] are s-values, the corner times are t_max * s. */
+void oracle_box_t(int kind, const double *q, const double I[6], double t_max,
+                  double m[3], double M[3])
 {
     int first = 1;
     for (int it = 0; it < 2; ++it)
         for (int iu = 0; iu < 2; ++iu)
             for (int iv = 0; iv < 2; ++iv) {
                 double F[3];
-                oracle_corner(kind, q, I[it], I[2 + iu], I[4 + iv], F);
+                oracle_corner(kind, q, t_max * I[it], I[2 + iu], I[4 + iv], F);
                 for (int c = 0; c < 3; ++c) {
                     if (first || F[c] < m[c]) m[c] = F[c];
                     if (first || F[c] > M[c]) M[c] = F[c];
@@ -91,15 +96,22 @@ void oracle_box(int kind, const double *q, const double I[6], double m[3],
             }
 }
 
-/* Eq. (kappas): kappa_t = 3 max_{u,v in {0,1}} ||F(0,u,v) - F(1,u,v)||_inf,
- * and likewise along u and v, over the corners of the domain [0,1]^3. */
-void oracle_kappa(int kind, const double *q, double kappa[3])
+void oracle_box(int kind, const double *q, const double I[6], double m[3],
+                double M[3])
+{
+    oracle_box_t(kind, q, I, 1.0, m, M);
+}
+
+/* Eq. (kappas): kappa_t = 3 max_{u,v in {0,1}} ||F(0,u,v) - F(t_max,u,v)||_inf,
+ * and likewise along u and v, over the corners of the domain
+ * [0,t_max] x [0,1]^2 (t_max = 1: the paper's [0,1]^3). */
+void oracle_kappa_t(int kind, const double *q, double t_max, double kappa[3])
 {
     double F[2][2][2][3];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c)
-                oracle_corner(kind, q, (double)a, (double)b, (double)c, F[a][b][c]);
+                oracle_corner(kind, q, t_max * (double)a, (double)b, (double)c, F[a][b][c]);
     double kt = 0.0, ku = 0.0, kv = 0.0;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
@@ -114,6 +126,11 @@ void oracle_kappa(int kind, const double *q, double kappa[3])
     kappa[0] = 3.0 * kt;
     kappa[1] = 3.0 * ku;
     kappa[2] = 3.0 * kv;
+}
+
+void oracle_kappa(int kind, const double *q, double kappa[3])
+{
+    oracle_kappa_t(kind, q, 1.0, kappa);
 }
 
 /* Eq. (ccd-error) and Eq. (msccd-error): eps^c = K gamma_c^3 with
@@ -222,12 +239,12 @@ static entry heap_pop(heap *h)
 /* Returns 1 (collision) or 0; -1 if memory for Q could not be obtained.
  * toi: left end of the recorded first colliding t-interval, or +inf.
  * out_tol: w(B) of the box checked at return, or 0.  checks: n. */
-int oracle_ccd(int kind, const double *q, const double err[3], double ms,
-               double delta, long long max_itr, int flags, double *toi,
-               double *out_tol, long long *checks)
+int oracle_ccd_t(int kind, const double *q, const double err[3], double ms,
+                 double delta, long long max_itr, double t_max, int flags,
+                 double *toi, double *out_tol, long long *checks)
 {
     double kappa[3];
-    oracle_kappa(kind, q, kappa);
+    oracle_kappa_t(kind, q, t_max, kappa);
 
     heap Q = {0};
     const double root[6] = {0.0, 1.0, 0.0, 1.0, 0.0, 1.0};
@@ -243,7 +260,7 @@ int oracle_ccd(int kind, const double *q, const double err[3], double ms,
         entry e = heap_pop(&Q);
         const double *I = e.I;
         double m[3], M[3];
-        oracle_box(kind, q, I, m, M);
+        oracle_box_t(kind, q, I, t_max, m, M);
         n += 1;
 
         /* B intersects C_eps: every axis interval, moved out by ms, meets
@@ -317,10 +334,18 @@ int oracle_ccd(int kind, const double *q, const double err[3], double ms,
         lp = e.level;
     }
     free(Q.a);
+    if (result == 1) r_toi = t_max * r_toi;   /* s -> t */
     if (toi) *toi = r_toi;
     if (out_tol) *out_tol = r_tol;
     if (checks) *checks = n;
     return result;
+}
+
+int oracle_ccd(int kind, const double *q, const double err[3], double ms,
+               double delta, long long max_itr, int flags, double *toi,
+               double *out_tol, long long *checks)
+{
+    return oracle_ccd_t(kind, q, err, ms, delta, max_itr, 1.0, flags, toi, out_tol, checks);
 }
 
 /* Batch driver: one oracle_ccd per query (queries are independent; OpenMP
@@ -328,11 +353,11 @@ int oracle_ccd(int kind, const double *q, const double err[3], double ms,
  * err: 3 doubles (err_stride 0) or n x 3 (err_stride 3).  Returns the number
  * of queries whose Q could not be allocated (their result is left as a
  * conservative collision at t = 0). */
-long long oracle_ccd_batch(int kind, const double *verts, long long n,
-                           const double *err, int err_stride, double ms,
-                           double delta, long long max_itr, int flags,
-                           unsigned char *collides, double *toi,
-                           double *out_tol, long long *checks, int nthreads)
+long long oracle_ccd_batch_t(int kind, const double *verts, long long n,
+                             const double *err, int err_stride, double ms,
+                             double delta, long long max_itr, double t_max, int flags,
+                             unsigned char *collides, double *toi,
+                             double *out_tol, long long *checks, int nthreads)
 {
     long long failures = 0;
     if (nthreads < 1) nthreads = 1;
@@ -340,8 +365,8 @@ long long oracle_ccd_batch(int kind, const double *verts, long long n,
     for (long long i = 0; i < n; ++i) {
         double t, w;
         long long c;
-        int r = oracle_ccd(kind, verts + 24 * i, err + (long long)err_stride * i,
-                           ms, delta, max_itr, flags, &t, &w, &c);
+        int r = oracle_ccd_t(kind, verts + 24 * i, err + (long long)err_stride * i,
+                             ms, delta, max_itr, t_max, flags, &t, &w, &c);
         if (r < 0) {
             failures += 1;
             r = 1; t = 0.0; w = INFINITY;
@@ -352,4 +377,14 @@ long long oracle_ccd_batch(int kind, const double *verts, long long n,
         if (checks) checks[i] = c;
     }
     return failures;
+}
+
+long long oracle_ccd_batch(int kind, const double *verts, long long n,
+                           const double *err, int err_stride, double ms,
+                           double delta, long long max_itr, int flags,
+                           unsigned char *collides, double *toi,
+                           double *out_tol, long long *checks, int nthreads)
+{
+    return oracle_ccd_batch_t(kind, verts, n, err, err_stride, ms, delta, max_itr, 1.0,
+                              flags, collides, toi, out_tol, checks, nthreads);
 }

@@ -38,16 +38,17 @@ def F(kind: int, q: Sequence[Fr], t: Fr, u: Fr, v: Fr) -> list[Fr]:
     return [((1 - u) * a[k] + u * b[k]) - ((1 - v) * c[k] + v * d[k]) for k in range(3)]
 
 
-def box(kind: int, q, I) -> tuple[list[Fr], list[Fr]]:
-    """Exact B_F(I): per-axis min / max over the 8 corners (Eq. box)."""
-    vals = [F(kind, q, t, u, v) for t in I[0:2] for u in I[2:4] for v in I[4:6]]
+def box(kind: int, q, I, t_max=1) -> tuple[list[Fr], list[Fr]]:
+    """Exact B_F(I): per-axis min / max over the 8 corners (Eq. box); I[0:2]
+    are s-values, the corner times t_max * s."""
+    vals = [F(kind, q, t * t_max, u, v) for t in I[0:2] for u in I[2:4] for v in I[4:6]]
     m = [min(x[k] for x in vals) for k in range(3)]
     M = [max(x[k] for x in vals) for k in range(3)]
     return m, M
 
 
-def kappa(kind: int, q) -> list[Fr]:
-    """Eq. (kappas) in exact arithmetic."""
+def kappa(kind: int, q, t_max=1) -> list[Fr]:
+    """Eq. (kappas) in exact arithmetic over [0, t_max] x [0,1]^2."""
     one, zero = Fr(1), Fr(0)
     out = []
     for dim in range(3):
@@ -59,15 +60,15 @@ def kappa(kind: int, q) -> list[Fr]:
                 others = [k for k in range(3) if k != dim]
                 lo[others[0]] = hi[others[0]] = i
                 lo[others[1]] = hi[others[1]] = j
-                A = F(kind, q, *lo)
-                B = F(kind, q, *hi)
+                A = F(kind, q, lo[0] * t_max, lo[1], lo[2])
+                B = F(kind, q, hi[0] * t_max, hi[1], hi[2])
                 best = max(best, max(abs(A[k] - B[k]) for k in range(3)))
         out.append(3 * best)
     return out
 
 
 def solve(kind: int, query, delta, max_itr: int, ms=0, err=(0, 0, 0),
-          literal_drop: bool = False):
+          literal_drop: bool = False, t_max=1):
     """Algorithm 2 in exact arithmetic.  Returns (collides, toi, w(B), checks).
 
     ``err`` is the per-axis half-width of C_eps (0 for a pure exact run);
@@ -79,14 +80,15 @@ def solve(kind: int, query, delta, max_itr: int, ms=0, err=(0, 0, 0),
     delta = Fr(delta)
     ms = Fr(ms)
     err = [Fr(e) for e in err]
-    kap = kappa(kind, q)
+    t_max = Fr(t_max)
+    kap = kappa(kind, q, t_max)
     Q = [(0, [Fr(0), Fr(1), Fr(0), Fr(1), Fr(0), Fr(1)])]
     n = 0
     lp = -1
     If_left = None
     while Q:
         level, I = Q.pop(0)
-        m, M = box(kind, q, I)
+        m, M = box(kind, q, I, t_max)
         n += 1
         hit = all(m[c] - ms <= err[c] and M[c] + ms >= -err[c] for c in range(3))
         if not hit:
@@ -96,11 +98,11 @@ def solve(kind: int, query, delta, max_itr: int, ms=0, err=(0, 0, 0),
             If_left = I[0]
         wB = max(M[c] - m[c] for c in range(3))
         if n >= max_itr:
-            return True, If_left, wB, n
+            return True, If_left * t_max, wB, n
         inside = all(m[c] - ms >= -err[c] and M[c] + ms <= err[c] for c in range(3))
         if wB < delta or inside:
             if first:
-                return True, If_left, wB, n
+                return True, If_left * t_max, wB, n
             if literal_drop:
                 lp = level
                 continue
@@ -109,7 +111,7 @@ def solve(kind: int, query, delta, max_itr: int, ms=0, err=(0, 0, 0),
         dim = 0 if c[0] == cm else (1 if c[1] == cm else 2)
         L, R = I[2 * dim], I[2 * dim + 1]
         if R - L <= Fr(1, 2**53):
-            return True, If_left, wB, n
+            return True, If_left * t_max, wB, n
         mid = (L + R) / 2
         I1, I2 = list(I), list(I)
         I1[2 * dim + 1] = mid

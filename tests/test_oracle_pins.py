@@ -430,3 +430,48 @@ def test_no_false_negative_vs_bruteforce_exact_roots(kind):
         assert c, "false negative against an exact root"
         assert toi <= float(first_root)
     assert found == 40
+
+
+# ---------------------------------------------------------------------------
+# SolveMSCCD's shortened time interval [0, t_max] (Sec. 6, line search)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("t_max", [0.5, 0.75])
+def test_shortened_interval_control_logic_matches_exact(kind, t_max):
+    rng = np.random.default_rng(90 + kind + int(8 * t_max))
+    for qv in _exact_grid_queries(rng, 20, kind):
+        zero = np.zeros(3)
+        for ms in (0.0, 1 / 64):
+            c, toi, tol, n = oracle.ccd(kind, qv, zero, ms=ms, delta=1 / 32, max_itr=400,
+                                        t_max=t_max)
+            cx, tx, wx, nx = ex.solve(kind, qv, Fr(1, 32), 400, ms=Fr(ms), t_max=Fr(t_max))
+            assert (c, n) == (cx, nx)
+            if c:
+                assert Fr(toi) == tx and Fr(tol) == wx and toi <= t_max
+
+
+def test_shortened_interval_sees_only_roots_before_t_max():
+    """Static triangle, point crossing its plane once at t*: a collision is
+    reported for t_max >= t* (toi <= t*), none for t_max well below t*."""
+    rng = np.random.default_rng(95)
+    g = 2.0**-20
+    for _ in range(40):
+        V = W.q(rng.uniform(-1, 1, (3, 3)), g)
+        t = W.q(rng.uniform(0.2, 0.8), 2.0**-10)
+        X = 0.5 * V[0] + 0.25 * V[1] + 0.25 * V[2]
+        nrm = np.cross(V[1] - V[0], V[2] - V[0])
+        nrm /= np.linalg.norm(nrm)
+        D = W.q(rng.uniform(2, 4) * nrm, g)
+        qv = np.concatenate([X - t * D, V.ravel(), X + (1 - t) * D, V.ravel()])
+        e = oracle.err_from_bounds(0, qv)
+        c1, toi1, _, _ = oracle.ccd(0, qv, e, t_max=1.0)
+        c2, toi2, _, _ = oracle.ccd(0, qv, e, t_max=min(1.0, t + 0.1))
+        c3, _, _, _ = oracle.ccd(0, qv, e, t_max=t - 0.1)
+        assert c1 and c2 and not c3
+        assert toi1 <= t and toi2 <= t
+    # t_max = 1 is the plain solver
+    b = W.unit_cube(1, 200, seed=96)
+    e = oracle.err_from_bounds(1, b.verts)
+    for x, y in zip(oracle.ccd_batch(1, b.verts, e), oracle.ccd_batch(1, b.verts, e, t_max=1.0)):
+        assert np.array_equal(x, y)
