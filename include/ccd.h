@@ -164,12 +164,16 @@ typedef struct {
     int64_t offset;   /* first query of the segment                          */
     int64_t count;    /* number of queries (>= 0)                            */
     int32_t kind;     /* CCD_KIND_VF or CCD_KIND_EE                          */
-    int32_t reserved; /* must be 0                                          */
+    int32_t group;    /* candidate set id >= 0, for ccd_group_reduce         */
     double err[3];    /* eps per axis for this segment (Eq. ccd-error)       */
     double ms;        /* minimum separation d >= 0 (Sec. 5.1)                */
     double delta;     /* tolerance delta > 0                                 */
     int64_t max_itr;  /* check limit m_I, 1 <= m_I <= the call's bound       */
-} ccd_segment;        /* 72 bytes, 8-byte aligned */
+    double t_max;     /* time interval [0, t_max], 0 < t_max <= 1: the
+                         shortened interval of SolveMSCCD (Sec. 6); the
+                         solver works in s in [0,1] with t = t_max * s
+                         rounded once, and toi = t_max * s_L               */
+} ccd_segment;        /* 80 bytes, 8-byte aligned */
 
 /*
  * Launch shapes of the solver kernels.  They change speed only: results are
@@ -196,9 +200,9 @@ size_t ccd_multi_workspace_bytes(int64_t n, int64_t max_itr_bound, const ccd_tun
  * max_itr_bound: an upper bound on every segment's max_itr, used to size the
  * deep frontier slots.  Outputs as for ccd_vf_batch, per query.  The
  * segment table is checked on the device: a table that does not tile
- * [0, n), or has a bad kind, delta <= 0, ms < 0, max_itr < 1 or max_itr >
- * max_itr_bound, sets the workspace status to CCD_ERR_ARG and no query is
- * answered.  Host-side errors as for ccd_vf_batch, plus CCD_ERR_ARG for
+ * [0, n), or has a bad kind, delta <= 0, ms < 0, max_itr < 1, max_itr >
+ * max_itr_bound, t_max outside (0, 1] or group < 0, sets the workspace
+ * status to CCD_ERR_ARG and no query is answered.  Host-side errors as for ccd_vf_batch, plus CCD_ERR_ARG for
  * nseg < 1 with n > 0, a NULL segs, or an invalid tuning.
  */
 ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
@@ -214,6 +218,19 @@ ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *se
  */
 ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segment *segs,
                                         int32_t nseg, void *stream);
+
+/*
+ * Line-search reduction per candidate set (Algorithm 4): for every group g
+ * of segments, alpha[g] = min toi and tol[g] = max out_tol over the group's
+ * queries (+inf and 0 for a group without collisions), from the outputs of
+ * a ccd_multi_batch over the same segment table.  The caller then takes
+ * alpha <- min(alpha, alpha[g]) and delta_i <- max(delta, tol[g]).  Segments
+ * whose group is >= ngroups are skipped.  All pointers are device pointers;
+ * alpha and tol hold ngroups doubles.
+ */
+ccd_status ccd_group_reduce(const double *toi, const double *out_tol, int64_t n,
+                            const ccd_segment *segs, int32_t nseg, int32_t ngroups,
+                            double *alpha, double *tol, void *stream);
 
 /*
  * Layout helper: copies n queries from an array of structures aos[n][24]

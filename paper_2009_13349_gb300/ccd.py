@@ -63,6 +63,9 @@ def lib():
         L.ccd_multi_batch.restype = ctypes.c_int
         L.ccd_segments_err_from_bounds.argtypes = [dp, i64, vp, ctypes.c_int32, vp]
         L.ccd_segments_err_from_bounds.restype = ctypes.c_int
+        L.ccd_group_reduce.argtypes = [dp, dp, i64, vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
+                                       vp]
+        L.ccd_group_reduce.restype = ctypes.c_int
         L.ccd_aos_to_soa.argtypes = [dp, i64, dp, i64, vp]
         L.ccd_aos_to_soa.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
@@ -213,9 +216,9 @@ def fp64_peak_probe(blocks: int, iters: int, stream=None):
 # ---- multi-instance batches -------------------------------------------------------
 
 SEGMENT_DTYPE = np.dtype([("offset", "<i8"), ("count", "<i8"), ("kind", "<i4"),
-                          ("reserved", "<i4"), ("err", "<f8", (3,)), ("ms", "<f8"),
-                          ("delta", "<f8"), ("max_itr", "<i8")])
-assert SEGMENT_DTYPE.itemsize == 72
+                          ("group", "<i4"), ("err", "<f8", (3,)), ("ms", "<f8"),
+                          ("delta", "<f8"), ("max_itr", "<i8"), ("t_max", "<f8")])
+assert SEGMENT_DTYPE.itemsize == 80
 
 
 class Tuning(ctypes.Structure):
@@ -235,7 +238,8 @@ def _tuning_ptr(tuning):
     return ctypes.pointer(tuning)
 
 
-def make_segments(counts, kinds, ms=0.0, delta=1e-6, max_itr=10**6, err=None) -> np.ndarray:
+def make_segments(counts, kinds, ms=0.0, delta=1e-6, max_itr=10**6, err=None, t_max=1.0,
+                  group=0) -> np.ndarray:
     """Host segment table (structured array) tiling [0, sum(counts))."""
     counts = np.asarray(counts, dtype=np.int64)
     k = len(counts)
@@ -246,6 +250,8 @@ def make_segments(counts, kinds, ms=0.0, delta=1e-6, max_itr=10**6, err=None) ->
     seg["ms"] = np.broadcast_to(np.asarray(ms, dtype=np.float64), (k,))
     seg["delta"] = np.broadcast_to(np.asarray(delta, dtype=np.float64), (k,))
     seg["max_itr"] = np.broadcast_to(np.asarray(max_itr, dtype=np.int64), (k,))
+    seg["t_max"] = np.broadcast_to(np.asarray(t_max, dtype=np.float64), (k,))
+    seg["group"] = np.broadcast_to(np.asarray(group, dtype=np.int32), (k,))
     if err is not None:
         seg["err"] = np.asarray(err, dtype=np.float64).reshape(k, 3)
     return seg
@@ -302,6 +308,20 @@ def multi_batch(verts: torch.Tensor, seg_dev: torch.Tensor, max_itr_bound: int,
                                  _stream(stream))
     _check(code, "ccd_multi_batch")
     return out
+
+
+def group_reduce(res: Result, seg_dev: torch.Tensor, ngroups: int, stream=None):
+    """Per candidate set: (alpha = min toi, tol = max out_tol) device tensors
+    of ngroups doubles (ccd_group_reduce)."""
+    n = res.toi.numel()
+    nseg = seg_dev.numel() // SEGMENT_DTYPE.itemsize
+    dev = res.toi.device
+    alpha = torch.empty(ngroups, dtype=torch.float64, device=dev)
+    tol = torch.empty(ngroups, dtype=torch.float64, device=dev)
+    _check(lib().ccd_group_reduce(_ptr(res.toi), _ptr(res.out_tol), n, _ptr(seg_dev), nseg,
+                                  int(ngroups), _ptr(alpha), _ptr(tol), _stream(stream)),
+           "ccd_group_reduce")
+    return alpha, tol
 
 
 def aos_to_soa(aos: torch.Tensor, soa: torch.Tensor, col: int = 0, stream=None) -> None:

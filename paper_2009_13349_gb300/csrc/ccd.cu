@@ -453,6 +453,7 @@ struct QP {
     double eps[3];
     double ms, delta;
     long long max_itr;
+    double t_max;    // time interval [0, t_max]: t = t_max * s (Sec. 6, SolveMSCCD)
 };
 
 __device__ __forceinline__ QP qp_single(const Params &p, long long i)
@@ -463,6 +464,7 @@ __device__ __forceinline__ QP qp_single(const Params &p, long long i)
     q.ms = p.ms;
     q.delta = p.delta;
     q.max_itr = p.max_itr;
+    q.t_max = 1.0;
     return q;
 }
 
@@ -484,15 +486,16 @@ __device__ __forceinline__ void root_query(const Params &p, long long i, const Q
     load_query(p.verts, p.n, i, Q);
     const double(&eps)[3] = q.eps;
 
-    // Corners of [0,1]^3.  At t = 0 the position x0 + dx*0 equals x0 and at
-    // t = 1 it is x0 + dx; with u, v in {0, 1} the products u e1, v e2 are
-    // 0 or the factor itself, so these are the fixed-order values of F.
+    // Corners of [0,t_max] x [0,1]^2.  At t = 0 the position x0 + dx*0 equals
+    // x0; at t = t_max it is x0 + dx*t_max (x0 + dx when t_max = 1); with u, v
+    // in {0, 1} the products u e1, v e2 are 0 or the factor itself, so these
+    // are the fixed-order values of F.
     double F[2][2][2][3];
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
         double P[12];
 #pragma unroll
-        for (int j = 0; j < 12; ++j) P[j] = it ? dadd(Q.x0[j], Q.dx[j]) : Q.x0[j];
+        for (int j = 0; j < 12; ++j) P[j] = it ? dadd(Q.x0[j], dmul(Q.dx[j], q.t_max)) : Q.x0[j];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (KIND == CCD_KIND_VF) {
@@ -647,7 +650,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             bsync<BS>();
             tqs += 2 * (unsigned long long)nrun;
             for (int task = tid; task < 2 * nrun; task += BS)
-                t_quantities<KIND>(Q, dyadic(s.run_at[task >> 1] + (task & 1), k[0]), tq + task * W);
+                t_quantities<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[task >> 1] + (task & 1), k[0])),
+                                   tq + task * W);
             bsync<BS>();
             if (valid) {
                 long long km[3], kM[3];
@@ -675,7 +679,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 const long long nfc = n_before + base + fc + 1;
                 if (nfc >= q.max_itr || term || !can_split) {
                     if (tid == 0) {
-                        write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, nfc);
+                        write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, nfc);
                         count_done(p, fallback, nfc, evals, tqs);
                     }
                     return true;
@@ -687,7 +691,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 const double w = s.cut_w;
                 bsync<BS>();
                 if (tid == 0) {
-                    write_result(p, qi, 1, dyadic(if_at, k[0]), w, n_before + base + cut + 1);
+                    write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), w,
+                                 n_before + base + cut + 1);
                     count_done(p, fallback, n_before + base + cut + 1, evals, tqs);
                 }
                 return true;
@@ -786,7 +791,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             }
             // answered as at the check limit: conservative, flagged
             if (tid == 0) {
-                write_result(p, qi, 1, dyadic(if_at, k[0]), first_w, n_before);
+                write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
                 count_done(p, true, n_before, evals, tqs);
@@ -829,7 +834,7 @@ __global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slot
 
 // ---- multi-instance (segmented) kernels ---------------------------------------
 
-static_assert(sizeof(ccd_segment) == 72, "ccd_segment layout");
+static_assert(sizeof(ccd_segment) == 80, "ccd_segment layout");
 
 // Segment of query i: the last segment whose offset is <= i.
 __device__ __forceinline__ int find_segment(const ccd_segment *segs, int nseg, long long i)
@@ -851,6 +856,7 @@ __device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
     q.ms = sg.ms;
     q.delta = sg.delta;
     q.max_itr = sg.max_itr;
+    q.t_max = sg.t_max;
     return q;
 }
 
@@ -862,7 +868,8 @@ __global__ void seg_validate_kernel(const ccd_segment *segs, int nseg, long long
     const ccd_segment g = segs[s];
     const long long start = s == 0 ? 0 : segs[s - 1].offset + segs[s - 1].count;
     bool ok = g.offset == start && g.count >= 0 && (g.kind == CCD_KIND_VF || g.kind == CCD_KIND_EE) &&
-              g.delta > 0.0 && g.ms >= 0.0 && g.max_itr >= 1 && g.max_itr <= max_itr_bound;
+              g.delta > 0.0 && g.ms >= 0.0 && g.max_itr >= 1 && g.max_itr <= max_itr_bound &&
+              g.t_max > 0.0 && g.t_max <= 1.0 && g.group >= 0;
     if (s == nseg - 1) ok = ok && g.offset + g.count == n;
     if (!ok) atomicExch(&hdr->status, (int)CCD_ERR_ARG);
 }
@@ -907,6 +914,55 @@ __global__ void __launch_bounds__(BS)
                 : solve_query<CCD_KIND_EE, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq);
         if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
         __syncthreads();
+    }
+}
+
+// Per candidate set (segment group): alpha = min toi, tol = max out_tol
+// (Algorithm 4: alpha <- min(t, alpha), delta_i <- max(delta_bar, delta_i)).
+// toi and out_tol are >= 0 (or +inf), so their bit patterns order like the
+// values and 64-bit atomicMin/atomicMax apply.
+__global__ void group_init_kernel(double *alpha, double *tol, int ngroups)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ngroups) {
+        alpha[g] = __longlong_as_double(0x7ff0000000000000LL);
+        tol[g] = 0.0;
+    }
+}
+
+__global__ void group_reduce_kernel(const double *__restrict__ toi,
+                                    const double *__restrict__ out_tol, long long n,
+                                    const ccd_segment *segs, int nseg, int ngroups,
+                                    double *alpha, double *tol)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        int grp = -1;
+        unsigned long long a = 0x7ff0000000000000ull, w = 0ull;
+        if (valid) {
+            grp = segs[find_segment(segs, nseg, i)].group;
+            if (grp >= ngroups) grp = -1;
+            a = (unsigned long long)__double_as_longlong(toi[i]);
+            w = (unsigned long long)__double_as_longlong(out_tol[i]);
+        }
+        const int g0 = __shfl_sync(FULL, grp, 0);
+        if (__all_sync(FULL, grp == g0)) {
+            for (int o = 16; o; o >>= 1) {
+                a = min(a, (unsigned long long)__shfl_xor_sync(FULL, a, o));
+                w = max(w, (unsigned long long)__shfl_xor_sync(FULL, w, o));
+            }
+            if (lane == 0 && g0 >= 0) {
+                atomicMin((unsigned long long *)&alpha[g0], a);
+                atomicMax((unsigned long long *)&tol[g0], w);
+            }
+        } else if (grp >= 0) {
+            atomicMin((unsigned long long *)&alpha[grp], a);
+            atomicMax((unsigned long long *)&tol[grp], w);
+        }
     }
 }
 
@@ -1427,6 +1483,25 @@ ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *se
 {
     return run_multi(verts, n, segs, nseg, max_itr_bound, collides, toi, out_tol, checks, tuning,
                      workspace, ws_bytes, stream);
+}
+
+ccd_status ccd_group_reduce(const double *toi, const double *out_tol, int64_t n,
+                            const ccd_segment *segs, int32_t nseg, int32_t ngroups,
+                            double *alpha, double *tol, void *stream)
+{
+    if (n < 0 || n >= 0x7fffffffLL || ngroups < 1 || !alpha || !tol ||
+        (n > 0 && (!toi || !out_tol || !segs || nseg < 1)))
+        return CCD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    group_init_kernel<<<(ngroups + 255) / 256, 256, 0, st>>>(alpha, tol, ngroups);
+    if (n > 0) {
+        const int sms = device_sms();
+        long long blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms) blocks = 8LL * sms;
+        group_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(toi, out_tol, n, segs, nseg,
+                                                             ngroups, alpha, tol);
+    }
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
 
 ccd_status ccd_aos_to_soa(const double *aos, int64_t n, double *soa, int64_t ld, void *stream)

@@ -142,3 +142,53 @@ def test_invalid_segment_table_reports_arg_error(ccd):
         ws = ccd.multi_workspace(v.shape[1], 1000)
         ccd.multi_batch(v, sd, 1000, ws=ws)
         assert ccd.workspace_status(ws)[0] == -1, broken
+
+
+def test_shortened_interval_matches_oracle(ccd):
+    """SolveMSCCD's time interval [0, t_max] (Sec. 6) per segment, including
+    non-dyadic t_max, against the oracle; t_max = 1 equals the plain call."""
+    wl = W.simulation_mixed(n=12_000, seed=31)
+    rng = np.random.default_rng(31)
+    parts, counts, kinds, tmaxes, mss = [], [], [], [], []
+    for b in wl.batches:
+        for t_max in (1.0, 0.5, 0.3, float(np.float64(1) / 3), 0.9876543210123):
+            idx = rng.choice(b.n, 800, replace=False)
+            parts.append(b.verts[idx])
+            counts.append(800)
+            kinds.append(b.kind)
+            tmaxes.append(t_max)
+            mss.append(float(rng.choice([0.0, 1e-4])))
+    verts = np.concatenate(parts)
+    seg = ccd.make_segments(counts, kinds, mss, 1e-6, 1_000_000, t_max=tmaxes)
+    v = ccd.to_soa(verts)
+    sd = ccd.segments_to_device(seg)
+    ccd.segments_err_from_bounds(v, sd)
+    seg = ccd.segments_from_device(sd)
+    got = _out(ccd.multi_batch(v, sd, 1_000_000))
+    for s in range(len(counts)):
+        o, c = int(seg["offset"][s]), int(seg["count"][s])
+        ref = oracle.ccd_batch(kinds[s], verts[o:o + c], seg["err"][s], ms=mss[s], delta=1e-6,
+                               max_itr=1_000_000, nthreads=NT, t_max=tmaxes[s])
+        _eq([x[o:o + c] for x in got], ref)
+        hit = ref[0] == 1
+        assert np.all(got[1][o:o + c][hit] <= tmaxes[s])
+
+
+def test_group_reduce_min_toi_max_tol(ccd):
+    wl, verts, counts, kinds, ms, delta, max_itr = _instances(count=6, total=30_000, seed=33)
+    k = len(counts)
+    groups = np.arange(k) % 3
+    seg = ccd.make_segments(counts, kinds, 0.0, 1e-6, 1_000_000, group=groups)
+    v = ccd.to_soa(verts)
+    sd = ccd.segments_to_device(seg)
+    ccd.segments_err_from_bounds(v, sd)
+    r = ccd.multi_batch(v, sd, 1_000_000)
+    alpha, tol = ccd.group_reduce(r, sd, 4)
+    torch.cuda.synchronize()
+    toi, ot = r.toi.cpu().numpy(), r.out_tol.cpu().numpy()
+    owner = np.repeat(groups, counts)
+    for g in range(4):
+        m = owner == g
+        want_a = toi[m].min() if m.any() else np.inf
+        want_t = ot[m].max() if m.any() else 0.0
+        assert alpha[g].item() == want_a and tol[g].item() == want_t
