@@ -33,6 +33,12 @@ METRIC = "CCD queries/sec FP64, 0 false negatives; p50/p99 batch latency; % FP64
 # t-quantity sets costs 2 t x 3 coords x (VF 10 / EE 12) + 3 (w(B)).
 T_OPS = {0: 24 + 9, 1: 24 + 6}
 BOX_OPS = {0: 2 * 3 * 10 + 3, 1: 2 * 3 * 12 + 3}
+# deep solver with shared partials: a u-partial (one t side) is VF q - u e1 /
+# EE p1 + u d1 (3 x 2 ops), a v-partial VF v e2 (3) / EE p3 + v d2 (6); a box
+# then needs only its 8 corner differences (24) and w(B) (3)
+A_OPS = {0: 6, 1: 6}
+B_OPS = {0: 3, 1: 6}
+SHARED_BOX_OPS = 24 + 3
 # the same check evaluated on its own (no sharing): 2 t-quantities + box
 OPS_PER_CHECK = {k: 2 * T_OPS[k] + BOX_OPS[k] for k in (0, 1)}
 
@@ -298,8 +304,14 @@ def run_native(args):
         naive = alg_ops
     else:
         sfx = "small" if top == 1 else "deep"
-        alg_ops = sum(counters[j]["tq_" + sfx] * T_OPS[b.kind] +
-                      counters[j]["evals_" + sfx] * BOX_OPS[b.kind] for j, b in enumerate(batches))
+        alg_ops = 0
+        for j, b in enumerate(batches):
+            c = counters[j]
+            shared = c["evals_shared_deep"] if sfx == "deep" else 0
+            alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * BOX_OPS[b.kind]
+                        + shared * SHARED_BOX_OPS)
+            if sfx == "deep":
+                alg_ops += c["a_tasks_deep"] * A_OPS[b.kind] + c["b_tasks_deep"] * B_OPS[b.kind]
         naive = sum(counters[j]["checks_" + sfx] * OPS_PER_CHECK[b.kind]
                     for j, b in enumerate(batches))
     achieved = alg_ops / (per_kernel[top] * 1e-3)

@@ -138,9 +138,11 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * of queries it handed on), [6] the same for the deep solver, [7] status,
  * [8] t-quantity evaluations (positions and edge vectors at one t, shared by
  * a run of boxes with equal t_L) by the small-frontier solver, [9] the same
- * for the deep solver.
+ * for the deep solver, [10] shared u-partials and [11] shared v-partials
+ * computed by the deep solver (one t side each), [12] deep box evaluations
+ * that used the shared partials.
  */
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], void *stream);
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[13], void *stream);
 
 /*
  * Optional stage timing for benchmarks: with count == 4, every following

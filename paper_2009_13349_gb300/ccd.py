@@ -186,11 +186,12 @@ def workspace_status(ws: torch.Tensor, stream=None):
 
 
 COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
-                 "evals_small", "evals_deep", "status", "tq_small", "tq_deep")
+                 "evals_small", "evals_deep", "status", "tq_small", "tq_deep", "a_tasks_deep",
+                 "b_tasks_deep", "evals_shared_deep")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
-    arr = (ctypes.c_int64 * 10)()
+    arr = (ctypes.c_int64 * 13)()
     _check(lib().ccd_workspace_counters(_ptr(ws), arr, _stream(stream)), "ccd_workspace_counters")
     return dict(zip(COUNTER_NAMES, list(arr)))
 

@@ -69,7 +69,10 @@ struct Header {
     unsigned long long evals_deep;    // box evaluations executed by the deep solver
     unsigned long long tq_small;      // t-quantity evaluations by the small solver
     unsigned long long tq_deep;       // t-quantity evaluations by the deep solver
-    int pad[44];
+    unsigned long long a_tasks_deep;  // shared u-partials (one t side each), deep solver
+    unsigned long long b_tasks_deep;  // shared v-partials (one t side each), deep solver
+    unsigned long long evals_shared_deep;  // deep box evaluations from shared partials
+    int pad[38];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -216,6 +219,34 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
             if (side == 0) { km[c] = lo; kM[c] = hi; }
             else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
         }
+    }
+}
+
+// One t side of corners_keys: accumulates the keys of the 4 corners at one t.
+template <int KIND>
+__device__ __forceinline__ void corners_keys_side(const double *T, double ul, double ur,
+                                                  double vl, double vr, bool first,
+                                                  long long (&km)[3], long long (&kM)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double f0, f1, f2, f3;
+        if (KIND == CCD_KIND_VF) {
+            const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
+            const double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
+            const double bl = dmul(vl, e2), br = dmul(vr, e2);
+            f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+        } else {
+            const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
+            const double al = dadd(a, dmul(ul, d1)), ar = dadd(a, dmul(ur, d1));
+            const double bl = dadd(b, dmul(vl, d2)), br = dadd(b, dmul(vr, d2));
+            f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+        }
+        const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
+        const long long lo = min(min(k0, k1), min(k2, k3));
+        const long long hi = max(max(k0, k1), max(k2, k3));
+        if (first) { km[c] = lo; kM[c] = hi; }
+        else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
     }
 }
 
@@ -432,6 +463,7 @@ __device__ __forceinline__ long long block_suffix_min(long long v, Smem<BS> &s)
 
 // ---- kernel parameters ------------------------------------------------------
 
+
 struct Params {
     const double *verts;
     long long n;
@@ -584,11 +616,192 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
 // colliding box of level l whose check index n was below m_I (otherwise the
 // query returned), so a level never holds more than 2 (m_I - 1) boxes.
 __device__ __forceinline__ void count_done(const Params &p, bool deep, long long n,
-                                           unsigned long long evals, unsigned long long tqs)
+                                           unsigned long long evals, unsigned long long tqs,
+                                           unsigned long long atasks = 0,
+                                           unsigned long long btasks = 0,
+                                           unsigned long long shared_evals = 0)
 {
     atomicAdd(deep ? &p.hdr->checks_deep : &p.hdr->checks_small, (unsigned long long)n);
     atomicAdd(deep ? &p.hdr->evals_deep : &p.hdr->evals_small, evals);
     atomicAdd(deep ? &p.hdr->tq_deep : &p.hdr->tq_small, tqs);
+    if (atasks | btasks | shared_evals) {
+        atomicAdd(&p.hdr->a_tasks_deep, atasks);
+        atomicAdd(&p.hdr->b_tasks_deep, btasks);
+        atomicAdd(&p.hdr->evals_shared_deep, shared_evals);
+    }
+}
+
+// ---- shared u/v partials for the deep solver ------------------------------------
+//
+// Within one chunk of a level, boxes of a run share t, and neighbouring boxes
+// share u or v values: per box there are about 0.6 distinct (run, u) and
+// (run, v) values on deep frontiers.  The corner expression splits into a
+// u-partial a(t,u) and a v-partial b(t,v) (VF: a = q - u e1, b = v e2,
+// F = a - b; EE: a = p1 + u d1, b = p3 + v d2, F = a - b), each the same
+// rounded operations the per-box evaluation performs, so computing every
+// distinct partial once per chunk gives bit-identical corners.  Distinct
+// keys (run, numerator) are found with shared-memory hash tables; dense ids
+// come from a block scan; partial tasks are packed into consecutive lanes.
+// A chunk with more than SH_RUN_CAP runs or SH_ENTRY_CAP distinct u or v
+// values is evaluated per box instead.
+constexpr int SH_RUN_CAP = 96;
+constexpr int SH_ENTRY_CAP = 320;
+constexpr int SH_SLOTS = 2048;                      // per table, power of two
+constexpr unsigned long long SH_EMPTY = ~0ull;
+constexpr unsigned long long SH_VAL_MASK = (1ull << 54) - 1;
+
+struct SharedUV {
+    unsigned long long ukey[SH_SLOTS], vkey[SH_SLOTS];
+    int uid[SH_SLOTS], vid[SH_SLOTS];
+    unsigned long long ukey_by_id[SH_ENTRY_CAP], vkey_by_id[SH_ENTRY_CAP];
+    double a[SH_ENTRY_CAP][2][3];
+    double b[SH_ENTRY_CAP][2][3];
+    double tq[2 * SH_RUN_CAP][12];
+};
+
+__device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long long key,
+                                         bool *inserted)
+{
+    // at most 2 * blockDim.x <= 1024 distinct keys in SH_SLOTS = 2048 slots,
+    // so probing always ends at the key or at an empty slot
+    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 53);
+    for (;;) {
+        const unsigned long long old = atomicCAS(&tab[h], SH_EMPTY, key);
+        if (old == SH_EMPTY) { *inserted = true; return (int)h; }
+        if (old == key) { *inserted = false; return (int)h; }
+        h = (h + 1) & (SH_SLOTS - 1);
+    }
+}
+
+// Per-box evaluation with private t-quantities (the fallback path).
+template <int KIND>
+__device__ __forceinline__ void eval_box_private(const Query &Q, const QP &q,
+                                                 const Thresholds &TH, const int (&k)[3],
+                                                 const Box &b, BoxTest &bt)
+{
+    constexpr int W = TWidth<KIND>::W;
+    const double ul = dyadic(b.a[1], k[1]), ur = dyadic(b.a[1] + 1, k[1]);
+    const double vl = dyadic(b.a[2], k[2]), vr = dyadic(b.a[2] + 1, k[2]);
+    long long km[3], kM[3];
+    double T[W];
+    t_quantities<KIND>(Q, dmul(q.t_max, dyadic(b.a[0], k[0])), T);
+    corners_keys_side<KIND>(T, ul, ur, vl, vr, true, km, kM);
+    t_quantities<KIND>(Q, dmul(q.t_max, dyadic(b.a[0] + 1, k[0])), T);
+    corners_keys_side<KIND>(T, ul, ur, vl, vr, false, km, kM);
+    box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
+}
+
+// One chunk (one box per thread) through shared u/v partials.
+template <int KIND, int BS>
+__device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
+                                                  const Thresholds &TH, const int (&k)[3],
+                                                  bool valid, const Box &b, long long nvalid,
+                                                  Smem<BS> &s, SharedUV &sh, BoxTest &bt,
+                                                  unsigned long long &tqs,
+                                                  unsigned long long &atasks,
+                                                  unsigned long long &btasks,
+                                                  unsigned long long &shared_evals)
+{
+    const int tid = threadIdx.x;
+    s.at[tid] = valid ? b.a[0] : ~0ull;
+    for (int j = tid; j < SH_SLOTS; j += BS) {
+        sh.ukey[j] = SH_EMPTY;
+        sh.vkey[j] = SH_EMPTY;
+    }
+    __syncthreads();
+    const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
+    int nrun;
+    const int before = block_excl_scan<BS>(start ? 1 : 0, &nrun, s);
+    const int run = before + (start ? 0 : -1);
+    if (nrun > SH_RUN_CAP) {                       // block-uniform
+        tqs += 2 * (unsigned long long)nvalid;
+        if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
+        return;
+    }
+    if (start) s.run_at[before] = b.a[0];
+    int su[2] = {0, 0}, sv[2] = {0, 0};
+    unsigned ins = 0;
+    unsigned long long ku[2] = {0, 0}, kv[2] = {0, 0};
+    if (valid) {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            bool fresh;
+            ku[d] = ((unsigned long long)run << 54) | (b.a[1] + d);
+            su[d] = sh_insert(sh.ukey, ku[d], &fresh);
+            if (fresh) ins |= 1u << d;
+            kv[d] = ((unsigned long long)run << 54) | (b.a[2] + d);
+            sv[d] = sh_insert(sh.vkey, kv[d], &fresh);
+            if (fresh) ins |= 4u << d;
+        }
+    }
+    __syncthreads();
+    int tot;
+    const int pack = block_excl_scan<BS>(__popc(ins & 3u) | (__popc(ins >> 2) << 16), &tot, s);
+    const int NU = tot & 0xffff, NV = tot >> 16;
+    const bool share = NU <= SH_ENTRY_CAP && NV <= SH_ENTRY_CAP;   // block-uniform
+    if (share) {
+        int iu = pack & 0xffff, iv = pack >> 16;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            if (ins & (1u << d)) { sh.uid[su[d]] = iu; sh.ukey_by_id[iu] = ku[d]; ++iu; }
+            if (ins & (4u << d)) { sh.vid[sv[d]] = iv; sh.vkey_by_id[iv] = kv[d]; ++iv; }
+        }
+        tqs += 2 * (unsigned long long)nrun;
+        for (int task = tid; task < 2 * nrun; task += BS)
+            t_quantities<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[task >> 1] + (task & 1), k[0])),
+                               sh.tq[task]);
+    }
+    __syncthreads();
+    if (!share) {
+        tqs += 2 * (unsigned long long)nvalid;
+        if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
+        return;
+    }
+    atasks += 2 * (unsigned long long)NU;
+    btasks += 2 * (unsigned long long)NV;
+    shared_evals += (unsigned long long)nvalid;
+    for (int task = tid; task < 2 * (NU + NV); task += BS) {
+        const int side = task & 1;
+        int e = task >> 1;
+        if (e < NU) {
+            const unsigned long long key = sh.ukey_by_id[e];
+            const double u = dyadic(key & SH_VAL_MASK, k[1]);
+            const double *T = sh.tq[2 * (int)(key >> 54) + side];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                sh.a[e][side][c] = KIND == CCD_KIND_VF ? dsub(T[c], dmul(u, T[3 + c]))
+                                                       : dadd(T[c], dmul(u, T[3 + c]));
+        } else {
+            e -= NU;
+            const unsigned long long key = sh.vkey_by_id[e];
+            const double v = dyadic(key & SH_VAL_MASK, k[2]);
+            const double *T = sh.tq[2 * (int)(key >> 54) + side];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                sh.b[e][side][c] = KIND == CCD_KIND_VF ? dmul(v, T[6 + c])
+                                                       : dadd(T[6 + c], dmul(v, T[9 + c]));
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        const int u0 = sh.uid[su[0]], u1 = sh.uid[su[1]];
+        const int v0 = sh.vid[sv[0]], v1 = sh.vid[sv[1]];
+        long long km[3], kM[3];
+#pragma unroll
+        for (int side = 0; side < 2; ++side)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double al = sh.a[u0][side][c], ar = sh.a[u1][side][c];
+                const double bl = sh.b[v0][side][c], br = sh.b[v1][side][c];
+                const long long k0 = dkey(dsub(al, bl)), k1 = dkey(dsub(al, br));
+                const long long k2 = dkey(dsub(ar, bl)), k3 = dkey(dsub(ar, br));
+                const long long lo = min(min(k0, k1), min(k2, k3));
+                const long long hi = max(max(k0, k1), max(k2, k3));
+                if (side == 0) { km[c] = lo; kM[c] = hi; }
+                else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
+            }
+        box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
+    }
 }
 
 template <int KIND, int BS>
@@ -598,6 +811,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
     unsigned long long tqs = 0;     // t-quantity evaluations (thread 0's tally)
+    unsigned long long atasks = 0, btasks = 0, shared_evals = 0;
     Query &Q = s.query;             // shared: only the per-run tasks read it
     if (tid < 12) {
         const double a = __ldg(p.verts + (size_t)tid * p.n + qi);
@@ -638,6 +852,11 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             Box b = Box{{0ull, 0ull, 0ull}};
             BoxTest bt{false, false, 0.0};
             if (valid) b = cur[i];
+            if (BS > 32) {
+                eval_chunk_shared<KIND, BS>(Q, q, TH, k, valid, b, min((long long)BS, size - base),
+                                            s, *(SharedUV *)tq, bt, tqs, atasks, btasks,
+                                            shared_evals);
+            } else {
             // Boxes are in Q order, so equal t_L form contiguous runs: the
             // t-quantities at t_L and t_R are computed once per run.
             s.at[tid] = valid ? b.a[0] : ~0ull;
@@ -660,6 +879,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                                    dyadic(b.a[2], k[2]), dyadic(b.a[2] + 1, k[2]), km, kM);
                 box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
             }
+            }
             evals += (unsigned long long)min((long long)BS, size - base);
             const long long nb = n_before + i + 1;
             const int fc = block_min<BS>(bt.hit ? tid : BIG, s);
@@ -680,7 +900,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 if (nfc >= q.max_itr || term || !can_split) {
                     if (tid == 0) {
                         write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, nfc);
-                        count_done(p, fallback, nfc, evals, tqs);
+                        count_done(p, fallback, nfc, evals, tqs, atasks, btasks, shared_evals);
                     }
                     return true;
                 }
@@ -693,7 +913,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 if (tid == 0) {
                     write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), w,
                                  n_before + base + cut + 1);
-                    count_done(p, fallback, n_before + base + cut + 1, evals, tqs);
+                    count_done(p, fallback, n_before + base + cut + 1, evals, tqs, atasks, btasks,
+                               shared_evals);
                 }
                 return true;
             }
@@ -707,7 +928,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
-                count_done(p, fallback, n_before + size, evals, tqs);
+                count_done(p, fallback, n_before + size, evals, tqs, atasks, btasks, shared_evals);
             }
             return true;
         }
@@ -783,10 +1004,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
         }
         if (nchild > cap) {
             if (!fallback) {
-                if (tid == 0) {
-                    atomicAdd(&p.hdr->evals_small, evals);
-                    atomicAdd(&p.hdr->tq_small, tqs);
-                }
+                if (tid == 0) count_done(p, false, 0, evals, tqs);
                 return false;
             }
             // answered as at the check limit: conservative, flagged
@@ -794,7 +1012,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
-                count_done(p, true, n_before, evals, tqs);
+                count_done(p, true, n_before, evals, tqs, atasks, btasks, shared_evals);
             }
             return true;
         }
@@ -835,6 +1053,7 @@ __global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slot
 // ---- multi-instance (segmented) kernels ---------------------------------------
 
 static_assert(sizeof(ccd_segment) == 80, "ccd_segment layout");
+static_assert(2 * 512 <= SH_SLOTS, "hash tables hold every key of a 512-box chunk");
 
 // Segment of query i: the last segment whose offset is <= i.
 __device__ __forceinline__ int find_segment(const ccd_segment *segs, int nseg, long long i)
@@ -887,7 +1106,7 @@ __global__ void __launch_bounds__(ROOT_THREADS)
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS)
+__global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
                      long long cap)
 {
@@ -1195,7 +1414,7 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
-    const size_t tq_deep = sizeof(double) * 2 * DEEP_THREADS * TWidth<KIND>::W;
+    const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
     if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
         cudaSuccess)
@@ -1283,7 +1502,7 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t 
     return CCD_OK;
 }
 
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], void *stream)
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[13], void *stream)
 {
     if (!workspace || !counters) return CCD_ERR_ARG;
     Header h;
@@ -1301,6 +1520,9 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[10], v
     counters[7] = h.status;
     counters[8] = (int64_t)h.tq_small;
     counters[9] = (int64_t)h.tq_deep;
+    counters[10] = (int64_t)h.a_tasks_deep;
+    counters[11] = (int64_t)h.b_tasks_deep;
+    counters[12] = (int64_t)h.evals_shared_deep;
     return CCD_OK;
 }
 
@@ -1397,7 +1619,7 @@ ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int ns
                                 size_t off_deep, int nb_deep, long long cap_deep, cudaStream_t st)
 {
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
-    const size_t tq_deep = sizeof(double) * 2 * DT * TWidth<CCD_KIND_EE>::W;
+    const size_t tq_deep = sizeof(SharedUV);
     if (cudaFuncSetAttribute(solve_kernel_seg<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tq_deep) != cudaSuccess)
         return CCD_ERR_CUDA;
@@ -1629,7 +1851,7 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
     root_kernel<CCD_KIND_VF><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_VF>::W;
-    const size_t tq_deep = sizeof(double) * 2 * DEEP_THREADS * TWidth<CCD_KIND_VF>::W;
+    const size_t tq_deep = sizeof(SharedUV);
     if (cudaFuncSetAttribute(solve_kernel<CCD_KIND_VF, DEEP_THREADS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
         cudaSuccess)
