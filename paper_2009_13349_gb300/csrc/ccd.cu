@@ -336,9 +336,22 @@ __device__ __forceinline__ long long warp_maxl(long long v)
     return v;
 }
 
+// Per-warp summary of one chunk's box tests, published before one barrier.
+struct WarpDecision {
+    int count;                 // colliding boxes in the warp
+    int first;                 // lane of the first colliding box (32: none)
+    int first_cut;             // lane of the first colliding box with n >= m_I
+    int term;                  // termination test of the first colliding box
+    unsigned long long at;     // a_t of the first colliding box
+    double w;                  // w(B) of the first colliding box
+    double w_cut;              // w(B) of the first cut box
+};
+
 template <int BS>
 struct Smem {
     Query query;                     // the query being solved
+    WarpDecision dec[BS / 32];
+    int scan_a[BS / 32], scan_b[BS / 32];
     unsigned long long at[BS];       // a_t of each thread's box in the chunk
     unsigned long long run_at[BS];   // a_t of each run of equal t_L
     int ired[BS / 32 + 1];
@@ -418,6 +431,35 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total, Smem<BS> &s)
     int before = __shfl_sync(0xffffffffu, wi - ws, warp);
     *total = __shfl_sync(0xffffffffu, wi, BS / 32 - 1);
     __syncthreads();
+    return before + inc - v;
+}
+
+// exclusive prefix sum with one barrier: `arr` must not be written again
+// before every thread has passed another barrier
+template <int BS>
+__device__ __forceinline__ int block_scan_1sync(int v, int *total, int *arr)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (BS == 32) {
+        *total = __shfl_sync(0xffffffffu, inc, 31);
+        return inc - v;
+    }
+    if (lane == 31) arr[warp] = inc;
+    __syncthreads();
+    int before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < BS / 32; ++w) {
+        const int x = arr[w];
+        before += (w < warp) ? x : 0;
+        tot += x;
+    }
+    *total = tot;
     return before + inc - v;
 }
 
@@ -711,7 +753,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     __syncthreads();
     const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
     int nrun;
-    const int before = block_excl_scan<BS>(start ? 1 : 0, &nrun, s);
+    const int before = block_scan_1sync<BS>(start ? 1 : 0, &nrun, s.scan_a);
     const int run = before + (start ? 0 : -1);
     if (nrun > SH_RUN_CAP) {                       // block-uniform
         tqs += 2 * (unsigned long long)nvalid;
@@ -736,7 +778,8 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     }
     __syncthreads();
     int tot;
-    const int pack = block_excl_scan<BS>(__popc(ins & 3u) | (__popc(ins >> 2) << 16), &tot, s);
+    const int pack =
+        block_scan_1sync<BS>(__popc(ins & 3u) | (__popc(ins >> 2) << 16), &tot, s.scan_b);
     const int NU = tot & 0xffff, NV = tot >> 16;
     const bool share = NU <= SH_ENTRY_CAP && NV <= SH_ENTRY_CAP;   // block-uniform
     if (share) {
@@ -882,46 +925,63 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             }
             evals += (unsigned long long)min((long long)BS, size - base);
             const long long nb = n_before + i + 1;
-            const int fc = block_min<BS>(bt.hit ? tid : BIG, s);
-            const int cut = block_min<BS>((bt.hit && nb >= q.max_itr) ? tid : BIG, s);
-            if (!found && fc != BIG) {
-                found = true;
-                if (tid == fc) {
-                    s.first_at = b.a[0];
-                    s.first_w = bt.w;
-                    s.first_term = bt.term;
+            // one barrier: each warp publishes its colliding count, its first
+            // colliding box (a_t, w(B), termination) and its first box past the
+            // check limit; every thread then derives the block-wide answers
+            {
+                const int lane = tid & 31, warp = tid >> 5;
+                const unsigned mh = __ballot_sync(0xffffffffu, bt.hit);
+                const unsigned mc = __ballot_sync(0xffffffffu, bt.hit && nb >= q.max_itr);
+                const int fh = mh ? __ffs(mh) - 1 : 32, fcl = mc ? __ffs(mc) - 1 : 32;
+                if (lane == 0) {
+                    s.dec[warp].count = __popc(mh);
+                    s.dec[warp].first = fh;
+                    s.dec[warp].first_cut = fcl;
                 }
+                if (lane == fh) {
+                    s.dec[warp].at = b.a[0];
+                    s.dec[warp].w = bt.w;
+                    s.dec[warp].term = bt.term;
+                }
+                if (lane == fcl) s.dec[warp].w_cut = bt.w;
                 bsync<BS>();
-                if_at = s.first_at;
-                first_w = s.first_w;
-                const bool term = s.first_term;
-                bsync<BS>();
-                const long long nfc = n_before + base + fc + 1;
-                if (nfc >= q.max_itr || term || !can_split) {
+                int before = 0, total = 0, wf = -1, wc = -1;
+#pragma unroll
+                for (int w = 0; w < BS / 32; ++w) {
+                    const int c = s.dec[w].count;
+                    before += (w < warp) ? c : 0;
+                    total += c;
+                    if (wf < 0 && c > 0) wf = w;
+                    if (wc < 0 && s.dec[w].first_cut < 32) wc = w;
+                }
+                if (!found && wf >= 0) {
+                    found = true;
+                    if_at = s.dec[wf].at;
+                    first_w = s.dec[wf].w;
+                    const long long nfc = n_before + base + wf * 32 + s.dec[wf].first + 1;
+                    if (nfc >= q.max_itr || s.dec[wf].term || !can_split) {
+                        if (tid == 0) {
+                            write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w,
+                                         nfc);
+                            count_done(p, fallback, nfc, evals, tqs, atasks, btasks,
+                                       shared_evals);
+                        }
+                        return true;
+                    }
+                }
+                if (wc >= 0) {   // a later colliding box reached the check limit
+                    const long long ncut = n_before + base + wc * 32 + s.dec[wc].first_cut + 1;
                     if (tid == 0) {
-                        write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, nfc);
-                        count_done(p, fallback, nfc, evals, tqs, atasks, btasks, shared_evals);
+                        write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])),
+                                     s.dec[wc].w_cut, ncut);
+                        count_done(p, fallback, ncut, evals, tqs, atasks, btasks, shared_evals);
                     }
                     return true;
                 }
+                const int pre = before + __popc(mh & ((1u << lane) - 1u));
+                if (bt.hit) cur[ncol + pre] = b;   // in-place compaction, ncol + pre <= i
+                ncol += total;
             }
-            if (cut != BIG) {   // a later colliding box reached the check limit
-                if (tid == cut) s.cut_w = bt.w;
-                bsync<BS>();
-                const double w = s.cut_w;
-                bsync<BS>();
-                if (tid == 0) {
-                    write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), w,
-                                 n_before + base + cut + 1);
-                    count_done(p, fallback, n_before + base + cut + 1, evals, tqs, atasks, btasks,
-                               shared_evals);
-                }
-                return true;
-            }
-            int total;
-            const int pre = block_excl_scan<BS>(bt.hit ? 1 : 0, &total, s);
-            if (bt.hit) cur[ncol + pre] = b;   // in-place compaction, ncol + pre <= i
-            ncol += total;
             bsync<BS>();
         }
         if (!found) {
@@ -1026,7 +1086,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 }
 
 template <int KIND, int BS>
-__global__ void __launch_bounds__(BS) solve_kernel(Params p, int deep, Box *slots, long long cap)
+__global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
+    solve_kernel(Params p, int deep, Box *slots, long long cap)
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
