@@ -256,7 +256,7 @@ def run_native(args):
         e.record(stream)
         return e
 
-    stage_sets = [[[new_event() for _ in range(4)] for _ in batches] for _ in range(args.steps)]
+    stage_sets = [[[new_event() for _ in range(5)] for _ in batches] for _ in range(args.steps)]
     marks = [new_event() for _ in range(args.steps + 1)]
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -275,11 +275,11 @@ def run_native(args):
     step_ms = [marks[s].elapsed_time(marks[s + 1]) for s in range(args.steps)]
     total_ms = marks[0].elapsed_time(marks[-1])
     total_ms = parallel.max_over_ranks(total_ms, device=dev)
-    stage_ms = np.zeros((len(batches), 3))
+    stage_ms = np.zeros((len(batches), 4))
     for s in range(args.steps):
         for j in range(len(batches)):
             ev = stage_sets[s][j]
-            for k in range(3):
+            for k in range(4):
                 stage_ms[j, k] += ev[k].elapsed_time(ev[k + 1]) / args.steps
     counters = [ccd.workspace_counters(w) for w in ws]
 
@@ -295,15 +295,21 @@ def run_native(args):
     checks = np.concatenate(checks)
 
     # roofline of the dominant kernel
-    names = ["root_kernel", "solve_kernel<32> (small frontier)", "solve_kernel<256> (deep)"]
+    names = ["root_kernel", "pool_kernel (pooled small frontiers)",
+             "solve_kernel<32> (one-warp frontier)", "solve_kernel<256> (deep)"]
     per_kernel = stage_ms.sum(axis=0)
     top = int(np.argmax(per_kernel))
     # executed FP64 arithmetic, from the kernel's own counters
     if top == 0:
         alg_ops = sum(b.n * OPS_PER_CHECK[b.kind] for b in batches)
         naive = alg_ops
+    elif top == 1:
+        alg_ops = sum(counters[j]["evals_pool"] * (2 * T_OPS[b.kind] + BOX_OPS[b.kind])
+                      for j, b in enumerate(batches))
+        naive = sum(counters[j]["checks_pool"] * OPS_PER_CHECK[b.kind]
+                    for j, b in enumerate(batches))
     else:
-        sfx = "small" if top == 1 else "deep"
+        sfx = "small" if top == 2 else "deep"
         alg_ops = 0
         for j, b in enumerate(batches):
             c = counters[j]
@@ -339,13 +345,13 @@ def run_native(args):
                                     "(one FP64 pipe op = one add or mul; -fmad=false)",
                      "work": "executed FP64 add/sub/mul from the kernel's counters",
                      "naive_equivalent_gflops": naive / (per_kernel[top] * 1e-3) / 1e9},
-        "stage_ms_per_step": {names[k]: float(per_kernel[k]) for k in range(3)},
+        "stage_ms_per_step": {names[k]: float(per_kernel[k]) for k in range(4)},
         "counters": {("VF" if b.kind == 0 else "EE"): counters[j] for j, b in enumerate(batches)},
         "checks": {"mean": float(checks.mean()), "p50": float(np.percentile(checks, 50)),
                    "p99": float(np.percentile(checks, 99)), "max": int(checks.max()),
                    "early_termination_pct": float(100.0 * np.mean(checks >= 10**6))},
         "false_negatives": fn, "toi_after_truth": toi_bad,
-        "gpu_launches": args.steps * len(batches) * 6,
+        "gpu_launches": args.steps * len(batches) * 7,
         "clocks": clk,
     }
 

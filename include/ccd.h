@@ -140,15 +140,21 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * a run of boxes with equal t_L) by the small-frontier solver, [9] the same
  * for the deep solver, [10] shared u-partials and [11] shared v-partials
  * computed by the deep solver (one t side each), [12] deep box evaluations
- * that used the shared partials.
+ * that used the shared partials, [13] queries the pooled solver handed to
+ * the one-warp solver, [14] sum of check counts n of queries finished by
+ * the pooled solver, [15] box evaluations executed by the pooled solver
+ * (each computes its own t-quantities at t_L and t_R).  The small-frontier
+ * solver of [3], [5], [8] is the one-warp solver.
  */
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[13], void *stream);
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[16], void *stream);
 
 /*
- * Optional stage timing for benchmarks: with count == 4, every following
+ * Optional stage timing for benchmarks: with count == 5, every following
  * batch call records events[0] before the level-0 kernel, events[1] after
- * it, events[2] after the small-frontier solver and events[3] after the
- * deep solver, on the call's stream.  The events (cudaEvent_t, created by
+ * it, events[2] after the pooled solver, events[3] after the one-warp
+ * solver and events[4] after the deep solver, on the call's stream
+ * (ccd_multi_batch has no pooled stage and records events[1] and [2]
+ * back to back).  The events (cudaEvent_t, created by
  * the caller) are not retained beyond the next ccd_set_stage_events call;
  * count == 0 switches recording off.  Process-wide; not thread-safe.
  */

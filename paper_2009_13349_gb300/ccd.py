@@ -187,23 +187,24 @@ def workspace_status(ws: torch.Tensor, stream=None):
 
 COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
                  "evals_small", "evals_deep", "status", "tq_small", "tq_deep", "a_tasks_deep",
-                 "b_tasks_deep", "evals_shared_deep")
+                 "b_tasks_deep", "evals_shared_deep", "mid_queries", "checks_pool",
+                 "evals_pool")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
-    arr = (ctypes.c_int64 * 13)()
+    arr = (ctypes.c_int64 * len(COUNTER_NAMES))()
     _check(lib().ccd_workspace_counters(_ptr(ws), arr, _stream(stream)), "ccd_workspace_counters")
     return dict(zip(COUNTER_NAMES, list(arr)))
 
 
 def set_stage_events(events) -> None:
-    """events: None (off) or 4 torch.cuda.Event(enable_timing=True), each
+    """events: None (off) or 5 torch.cuda.Event(enable_timing=True), each
     already recorded once (so that its CUDA handle exists)."""
     if not events:
         _check(lib().ccd_set_stage_events(None, 0), "ccd_set_stage_events")
         return
-    arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
-    _check(lib().ccd_set_stage_events(arr, 4), "ccd_set_stage_events")
+    arr = (ctypes.c_void_p * 5)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    _check(lib().ccd_set_stage_events(arr, 5), "ccd_set_stage_events")
 
 
 def fp64_peak_probe(blocks: int, iters: int, stream=None):

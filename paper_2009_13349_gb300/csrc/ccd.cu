@@ -46,6 +46,9 @@ constexpr int ROOT_THREADS = 256;
 constexpr int SMALL_THREADS = 32;     // one warp per query
 constexpr int SMALL_BLOCKS_PER_SM = 16;
 constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
+constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
+constexpr int POOL_CAP = 64;          // ... boxes per level per query ...
+constexpr int POOL_BLOCKS_PER_SM = 8; // ... and one-warp blocks per SM
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM
 constexpr int BIG = 0x7fffffff;
@@ -62,7 +65,8 @@ struct Header {
     int head_deep;   // work counter of the deep solver
     int status;      // CCD_OK or CCD_ERR_CAPACITY
     int fallbacks;   // queries answered by the capacity fallback
-    int pad0[2];
+    int mid;         // queries handed from the pooled solver to the one-warp solver
+    int head_pool;   // work counter of the pooled solver
     unsigned long long checks_small;  // sum of n over queries finished by the small solver
     unsigned long long checks_deep;   // sum of n over queries finished by the deep solver
     unsigned long long evals_small;   // box evaluations executed by the small solver
@@ -72,13 +76,15 @@ struct Header {
     unsigned long long a_tasks_deep;  // shared u-partials (one t side each), deep solver
     unsigned long long b_tasks_deep;  // shared v-partials (one t side each), deep solver
     unsigned long long evals_shared_deep;  // deep box evaluations from shared partials
-    int pad[38];
+    unsigned long long checks_pool;   // sum of n over queries finished by the pooled solver
+    unsigned long long evals_pool;    // box evaluations executed by the pooled solver
+    int pad[34];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
 struct Layout {
-    size_t off_surv, off_over, off_kappa, off_small, off_deep, total;
-    int nb_small, nb_deep;
+    size_t off_surv, off_mid, off_over, off_kappa, off_pool, off_small, off_deep, total;
+    int nb_pool, nb_small, nb_deep;
     long long cap_small, cap_deep;
 };
 
@@ -517,8 +523,9 @@ struct Params {
     double *toi, *out_tol;
     long long *checks;
     Header *hdr;
-    int *surv;
-    int *over;
+    int *surv;       // level-0 survivors           -> pooled solver
+    int *mid;        // pooled solver hand-offs     -> one-warp solver
+    int *over;       // one-warp solver hand-offs   -> deep solver
     double *kappa;
 };
 
@@ -1085,18 +1092,19 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
     }
 }
 
+// Persistent: blocks take queries from `list` (length *count, work counter
+// *head); a query whose frontier outgrows `cap` goes to out_list (one-warp
+// tier only; the deep tier answers it through the capacity fallback).
 template <int KIND, int BS>
 __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
-    solve_kernel(Params p, int deep, Box *slots, long long cap)
+    solve_kernel(Params p, int deep, Box *slots, long long cap, const int *list,
+                 const int *count, int *head, int *out_list, int *out_count)
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
     extern __shared__ double tq[];   // [2 * BS][TWidth<KIND>::W] t-quantities
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
-    const int *list = deep ? p.over : p.surv;
-    const int *count = deep ? &p.hdr->overflow : &p.hdr->survivors;
-    int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(head, 1);
         __syncthreads();
@@ -1106,9 +1114,234 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
         const long long qi = list[idx];
         const bool done =
             solve_query<KIND, BS>(p, qp_single(p, qi), qi, cur, nxt, cap, deep != 0, s, tq);
-        if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
+        if (!done && threadIdx.x == 0) out_list[atomicAdd(out_count, 1)] = (int)qi;
         __syncthreads();
     }
+}
+
+// ---- pooled solver (small frontiers, many queries per warp) -------------------
+//
+// An FP64 warp-instruction costs the same for 1 or 32 active lanes, and most
+// surviving queries have only a few boxes per level.  A warp here holds up
+// to POOL_SLOTS queries ("slots") and, every iteration, packs the next boxes
+// of all its slots' current levels into its 32 lanes (slot priority rotates
+// so that no slot waits long), evaluates them with the same code path, then
+// lets each slot's owner lane apply Algorithm 2's sequential bookkeeping to
+// its boxes in Q order: first colliding box, check limit, termination,
+// children appended in Q order (u/v splits: left then right; t splits: the
+// right children of a run of equal t_L wait in a pending list flushed when
+// the run ends).  A level with more than POOL_CAP children hands the query
+// to the one-warp solver, which restarts it.
+struct PoolSlot {
+    long long qi, size, pos, n_before;
+    unsigned long long if_at, pend_at;
+    double first_w;
+    int k[3], sd, can_split, found, nn, np, buf;
+};
+
+struct PoolShared {
+    PoolSlot st[POOL_SLOTS];
+    Query Q[POOL_SLOTS];
+    QP qp[POOL_SLOTS];
+    Thresholds TH[POOL_SLOTS];
+    double kap[POOL_SLOTS][3];
+    Box box[32];
+    double w[32];
+    int hit[32], term[32], lane_slot[32], lane_off[32];
+};
+
+__device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[3])
+{
+    const double ct = dmul(pow2neg(S.k[0]), kap[0]);
+    const double cu = dmul(pow2neg(S.k[1]), kap[1]);
+    const double cv = dmul(pow2neg(S.k[2]), kap[2]);
+    double cm = ct;
+    if (cu > cm) cm = cu;
+    if (cv > cm) cm = cv;
+    S.sd = (ct == cm) ? 0 : (cu == cm) ? 1 : 2;
+    S.can_split = S.k[S.sd] < KMAX;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ PoolShared sh;
+    const int lane = threadIdx.x;
+    PoolSlot &S = sh.st[lane];                     // the slot this lane owns
+    Box *const mine = mem + ((size_t)blockIdx.x * POOL_SLOTS + lane) * 3 * (size_t)cap;
+    const int count = *(volatile const int *)&p.hdr->survivors;
+    bool drained = false;
+    unsigned long long evals = 0, checks_done = 0;
+    int rot = 0;
+    S.qi = -1;
+    __syncwarp();
+
+    for (;;) {
+        // 1. empty slots take the next survivors (warp-aggregated)
+        const bool empty = S.qi < 0;
+        const unsigned want = __ballot_sync(FULL, empty && !drained);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&p.hdr->head_pool, __popc(want));
+            base = __shfl_sync(FULL, base, leader);
+            if (empty && !drained) {
+                const int idx = base + __popc(want & ((1u << lane) - 1u));
+                if (idx < count) {
+                    const long long qi = p.surv[idx];
+                    load_query(p.verts, p.n, qi, sh.Q[lane]);
+                    sh.qp[lane] = qp_single(p, qi);
+                    make_thresholds(sh.qp[lane].eps, sh.qp[lane].delta, sh.TH[lane]);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) sh.kap[lane][c] = p.kappa[3 * qi + c];
+                    S.qi = qi;
+                    S.size = 1;
+                    S.pos = 0;
+                    S.n_before = 0;
+                    S.found = 0;
+                    S.nn = S.np = 0;
+                    S.buf = 0;
+                    S.k[0] = S.k[1] = S.k[2] = 0;
+                    pool_split_dim(S, sh.kap[lane]);
+                    mine[0] = Box{{0ull, 0ull, 0ull}};
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        __syncwarp();
+        const bool active = S.qi >= 0;
+        if (!__any_sync(FULL, active)) break;
+
+        // 2. place the slots' next boxes in the lanes, rotating the priority
+        const int rem = active ? (int)min(S.size - S.pos, 32LL) : 0;
+        const int rrem = __shfl_sync(FULL, rem, (lane + rot) & 31);
+        int inc = rrem;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        const int E = __shfl_sync(FULL, inc - rrem, (lane - rot) & 31);
+        const int take = (active && E < 32) ? min(rem, 32 - E) : 0;
+        for (int j = 0; j < take; ++j) {
+            sh.lane_slot[E + j] = lane;
+            sh.lane_off[E + j] = j;
+        }
+        rot = (rot + 1) & 31;
+        __syncwarp();
+
+        // 3. one box per lane
+        const int nbox = min(total, 32);
+        BoxTest bt{false, false, 0.0};
+        Box b = Box{{0ull, 0ull, 0ull}};
+        if (lane < nbox) {
+            const int so = sh.lane_slot[lane];
+            const PoolSlot &T = sh.st[so];
+            const Box *cur = mem + ((size_t)blockIdx.x * POOL_SLOTS + so) * 3 * (size_t)cap +
+                             (T.buf ? cap : 0);
+            b = cur[T.pos + sh.lane_off[lane]];
+            eval_box_private<KIND>(sh.Q[so], sh.qp[so], sh.TH[so], T.k, b, bt);
+            evals += 1;
+        }
+        sh.box[lane] = b;
+        sh.hit[lane] = bt.hit;
+        sh.term[lane] = bt.term;
+        sh.w[lane] = bt.w;
+        __syncwarp();
+
+        // 4. the owner lane applies Algorithm 2 to its boxes, in Q order
+        if (take > 0) {
+            const QP &qq = sh.qp[lane];
+            Box *cur = mine + (S.buf ? cap : 0);
+            Box *nxt = mine + (S.buf ? 0 : cap);
+            Box *pend = mine + 2 * (size_t)cap;
+            (void)cur;
+            int outcome = 0;   // 0 continue, 1 answered, 2 hand over
+            long long n = 0;
+            for (int L = E; L < E + take; ++L) {
+                n = S.n_before + S.pos + (L - E) + 1;
+                if (!sh.hit[L]) continue;
+                const Box bb = sh.box[L];
+                if (!S.found) {
+                    S.found = 1;
+                    S.if_at = bb.a[0];
+                    S.first_w = sh.w[L];
+                    if (n >= qq.max_itr || sh.term[L] || !S.can_split) {
+                        write_result(p, S.qi, 1, dmul(qq.t_max, dyadic(S.if_at, S.k[0])),
+                                     sh.w[L], n);
+                        outcome = 1;
+                        break;
+                    }
+                } else if (n >= qq.max_itr) {
+                    write_result(p, S.qi, 1, dmul(qq.t_max, dyadic(S.if_at, S.k[0])), sh.w[L], n);
+                    outcome = 1;
+                    break;
+                }
+                if (S.sd == 0) {
+                    if (S.np > 0 && S.pend_at != bb.a[0]) {
+                        for (int j = 0; j < S.np; ++j) nxt[S.nn + j] = pend[j];
+                        S.nn += S.np;
+                        S.np = 0;
+                    }
+                    if (S.nn + S.np + 2 > cap) { outcome = 2; break; }
+                    nxt[S.nn++] = Box{{2 * bb.a[0], bb.a[1], bb.a[2]}};
+                    pend[S.np++] = Box{{2 * bb.a[0] + 1, bb.a[1], bb.a[2]}};
+                    S.pend_at = bb.a[0];
+                } else {
+                    const int sd = S.sd;
+                    bool keep_r = true;
+                    if (KIND == CCD_KIND_VF) {
+                        const int ku = S.k[1] + (sd == 1), kv = S.k[2] + (sd == 2);
+                        const unsigned long long au = sd == 1 ? 2 * bb.a[1] + 1 : bb.a[1];
+                        const unsigned long long av = sd == 2 ? 2 * bb.a[2] + 1 : bb.a[2];
+                        const int K = ku > kv ? ku : kv;
+                        keep_r = (au << (K - ku)) + (av << (K - kv)) <= (1ull << K);
+                    }
+                    if (S.nn + 1 + (keep_r ? 1 : 0) > cap) { outcome = 2; break; }
+                    Box l = bb, r = bb;
+                    l.a[sd] = 2 * bb.a[sd];
+                    r.a[sd] = 2 * bb.a[sd] + 1;
+                    nxt[S.nn++] = l;
+                    if (keep_r) nxt[S.nn++] = r;
+                }
+            }
+            if (outcome == 1) {
+                checks_done += (unsigned long long)n;
+                S.qi = -1;
+            } else if (outcome == 2) {
+                p.mid[atomicAdd(&p.hdr->mid, 1)] = (int)S.qi;
+                S.qi = -1;
+            } else {
+                S.pos += take;
+                if (S.pos == S.size) {
+                    for (int j = 0; j < S.np; ++j) nxt[S.nn + j] = pend[j];
+                    S.nn += S.np;
+                    S.np = 0;
+                    if (!S.found) {
+                        write_result(p, S.qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
+                                     S.n_before + S.size);
+                        checks_done += (unsigned long long)(S.n_before + S.size);
+                        S.qi = -1;
+                    } else {
+                        S.n_before += S.size;
+                        S.buf ^= 1;
+                        S.size = S.nn;
+                        S.nn = 0;
+                        S.k[S.sd] += 1;
+                        S.pos = 0;
+                        S.found = 0;
+                        pool_split_dim(S, sh.kap[lane]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    atomicAdd(&p.hdr->evals_pool, evals);
+    atomicAdd(&p.hdr->checks_pool, checks_done);
 }
 
 // ---- multi-instance (segmented) kernels ---------------------------------------
@@ -1402,8 +1635,12 @@ Layout layout_fixed(long long n, int sms)
     Layout L{};
     size_t off = align256(sizeof(Header));
     L.off_surv = off; off = align256(off + sizeof(int) * (size_t)n);
+    L.off_mid = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_over = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_kappa = off; off = align256(off + 3 * sizeof(double) * (size_t)n);
+    L.nb_pool = sms * POOL_BLOCKS_PER_SM;
+    L.off_pool = off;
+    off = align256(off + sizeof(Box) * 3 * (size_t)POOL_CAP * POOL_SLOTS * (size_t)L.nb_pool);
     L.nb_small = sms * SMALL_BLOCKS_PER_SM;
     L.cap_small = SMALL_CAP;
     L.off_small = off; off = align256(off + sizeof(Box) * 2 * (size_t)SMALL_CAP * L.nb_small);
@@ -1433,7 +1670,7 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
     return true;
 }
 
-cudaEvent_t g_stage_events[4];
+cudaEvent_t g_stage_events[5];
 int g_stage_events_on = 0;
 
 inline void stage_mark(int i, cudaStream_t st)
@@ -1467,13 +1704,17 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
     p.hdr = (Header *)ws;
     p.surv = (int *)(ws + L.off_surv);
+    p.mid = (int *)(ws + L.off_mid);
     p.over = (int *)(ws + L.off_over);
     p.kappa = (double *)(ws + L.off_kappa);
+    Header *h = p.hdr;
 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
     stage_mark(0, st);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
+    pool_kernel<KIND><<<L.nb_pool, 32, 0, st>>>(p, (Box *)(ws + L.off_pool), POOL_CAP);
+    stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
     const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
     if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
@@ -1481,11 +1722,13 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
         cudaSuccess)
         return CCD_ERR_CUDA;
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
-        p, 0, (Box *)(ws + L.off_small), L.cap_small);
-    stage_mark(2, st);
-    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, tq_deep, st>>>(
-        p, 1, (Box *)(ws + L.off_deep), L.cap_deep);
+        p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
+        &h->overflow);
     stage_mark(3, st);
+    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, tq_deep, st>>>(
+        p, 1, (Box *)(ws + L.off_deep), L.cap_deep, p.over, &h->overflow, &h->head_deep, nullptr,
+        nullptr);
+    stage_mark(4, st);
     if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
     return CCD_OK;
 }
@@ -1563,7 +1806,7 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t 
     return CCD_OK;
 }
 
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[13], void *stream)
+ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[16], void *stream)
 {
     if (!workspace || !counters) return CCD_ERR_ARG;
     Header h;
@@ -1584,6 +1827,9 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[13], v
     counters[10] = (int64_t)h.a_tasks_deep;
     counters[11] = (int64_t)h.b_tasks_deep;
     counters[12] = (int64_t)h.evals_shared_deep;
+    counters[13] = h.mid;
+    counters[14] = (int64_t)h.checks_pool;
+    counters[15] = (int64_t)h.evals_pool;
     return CCD_OK;
 }
 
@@ -1593,8 +1839,8 @@ ccd_status ccd_set_stage_events(void *const *events, int count)
         g_stage_events_on = 0;
         return CCD_OK;
     }
-    if (count != 4 || !events) return CCD_ERR_ARG;
-    for (int i = 0; i < 4; ++i) {
+    if (count != 5 || !events) return CCD_ERR_ARG;
+    for (int i = 0; i < 5; ++i) {
         if (!events[i]) return CCD_ERR_ARG;
         g_stage_events[i] = (cudaEvent_t)events[i];
     }
@@ -1684,12 +1930,13 @@ ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int ns
     if (cudaFuncSetAttribute(solve_kernel_seg<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tq_deep) != cudaSuccess)
         return CCD_ERR_CUDA;
+    stage_mark(2, st);   // no pooled stage in the multi-instance path
     solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
         p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
-    stage_mark(2, st);
+    stage_mark(3, st);
     solve_kernel_seg<DT><<<nb_deep, DT, tq_deep, st>>>(p, segs, nseg, 1, (Box *)(ws + off_deep),
                                                        cap_deep);
-    stage_mark(3, st);
+    stage_mark(4, st);
     return CCD_OK;
 }
 
@@ -1723,6 +1970,7 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     p.hdr = (Header *)ws;
     size_t off = align256(sizeof(Header));
     p.surv = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.mid = nullptr;
     p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
     const size_t off_small = off;
@@ -1906,8 +2154,10 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
     p.hdr = (Header *)ws;
     p.surv = (int *)(ws + STATIC_OFF_SURV);
+    p.mid = nullptr;
     p.over = (int *)(ws + STATIC_OFF_OVER);
     p.kappa = (double *)(ws + STATIC_OFF_KAPPA);
+    Header *h = p.hdr;
 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
     root_kernel<CCD_KIND_VF><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
@@ -1918,8 +2168,10 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
         cudaSuccess)
         return CCD_ERR_CUDA;
     solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<STATIC_SMALL_BLOCKS, SMALL_THREADS, tq_small, st>>>(
-        p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP);
+        p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP, p.surv, &h->survivors,
+        &h->head_small, p.over, &h->overflow);
     solve_kernel<CCD_KIND_VF, DEEP_THREADS><<<STATIC_DEEP_SLOTS, DEEP_THREADS, tq_deep, st>>>(
-        p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP);
+        p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP, p.over, &h->overflow, &h->head_deep,
+        nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
