@@ -683,18 +683,22 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 // ---- shared u/v partials for the deep solver ------------------------------------
 //
 // Within one chunk of a level, boxes of a run share t, and neighbouring boxes
-// share u or v values: per box there are about 0.6 distinct (run, u) and
-// (run, v) values on deep frontiers.  The corner expression splits into a
-// u-partial a(t,u) and a v-partial b(t,v) (VF: a = q - u e1, b = v e2,
-// F = a - b; EE: a = p1 + u d1, b = p3 + v d2, F = a - b), each the same
-// rounded operations the per-box evaluation performs, so computing every
-// distinct partial once per chunk gives bit-identical corners.  Distinct
-// keys (run, numerator) are found with shared-memory hash tables; dense ids
-// come from a block scan; partial tasks are packed into consecutive lanes.
-// A chunk with more than SH_RUN_CAP runs or SH_ENTRY_CAP distinct u or v
-// values is evaluated per box instead.
+// share u or v values.  The corner expression splits into a u-partial
+// a(t,u) and a v-partial b(t,v) (VF: a = q - u e1, b = v e2, F = a - b;
+// EE: a = p1 + u d1, b = p3 + v d2, F = a - b), each the same rounded
+// operations the per-box evaluation performs, so computing every distinct
+// partial once per chunk gives bit-identical corners.  Partials are keyed by
+// (t value, numerator): the chunk's boxes are in Q order (ascending t_L), so
+// its distinct t values are the runs' left ends plus the right ends that are
+// not the next run's left end, and their dense ids follow from one block
+// scan (t_L of run r has id r + gaps up to r; t_R has that id + 1).  Distinct
+// keys are found with shared-memory hash tables; dense partial ids come from
+// a second block scan; tasks are packed into consecutive lanes.  A chunk
+// with more than SH_RUN_CAP runs or SH_ENTRY_CAP distinct u or v partials is
+// evaluated per box instead.
 constexpr int SH_RUN_CAP = 96;
-constexpr int SH_ENTRY_CAP = 320;
+constexpr int SH_TV_CAP = 2 * SH_RUN_CAP;           // distinct t values per chunk
+constexpr int SH_ENTRY_CAP = 640;                   // partials per table (one t value each)
 constexpr int SH_SLOTS = 2048;                      // per table, power of two
 constexpr unsigned long long SH_EMPTY = ~0ull;
 constexpr unsigned long long SH_VAL_MASK = (1ull << 54) - 1;
@@ -703,16 +707,16 @@ struct SharedUV {
     unsigned long long ukey[SH_SLOTS], vkey[SH_SLOTS];
     int uid[SH_SLOTS], vid[SH_SLOTS];
     unsigned long long ukey_by_id[SH_ENTRY_CAP], vkey_by_id[SH_ENTRY_CAP];
-    double a[SH_ENTRY_CAP][2][3];
-    double b[SH_ENTRY_CAP][2][3];
-    double tq[2 * SH_RUN_CAP][12];
+    double a[SH_ENTRY_CAP][3];
+    double b[SH_ENTRY_CAP][3];
+    double tq[SH_TV_CAP][12];
 };
 
 __device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long long key,
                                          bool *inserted)
 {
-    // at most 2 * blockDim.x <= 1024 distinct keys in SH_SLOTS = 2048 slots,
-    // so probing always ends at the key or at an empty slot
+    // at most 4 * blockDim.x <= SH_SLOTS distinct keys per chunk (half full for
+    // 256 threads), so probing always ends at the key or at an empty slot
     unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 53);
     for (;;) {
         const unsigned long long old = atomicCAS(&tab[h], SH_EMPTY, key);
@@ -751,6 +755,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
                                                   unsigned long long &btasks,
                                                   unsigned long long &shared_evals)
 {
+    static_assert(4 * BS <= SH_SLOTS, "every insert finds its key or an empty slot");
     const int tid = threadIdx.x;
     s.at[tid] = valid ? b.a[0] : ~0ull;
     for (int j = tid; j < SH_SLOTS; j += BS) {
@@ -758,48 +763,53 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         sh.vkey[j] = SH_EMPTY;
     }
     __syncthreads();
+    // runs of equal t_L, and gaps between consecutive runs' t values
     const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
-    int nrun;
-    const int before = block_scan_1sync<BS>(start ? 1 : 0, &nrun, s.scan_a);
-    const int run = before + (start ? 0 : -1);
+    const bool gap = start && tid > 0 && s.at[tid - 1] + 1 != b.a[0];
+    const bool open_r = valid && (tid + 1 >= nvalid || (s.at[tid + 1] != b.a[0] &&
+                                                         s.at[tid + 1] != b.a[0] + 1));
+    int tot;
+    const int pk = block_scan_1sync<BS>((start ? 1 : 0) | ((gap ? 1 : 0) << 16), &tot, s.scan_a);
+    const int nrun = tot & 0xffff, ntv = nrun + (tot >> 16) + 1;
     if (nrun > SH_RUN_CAP) {                       // block-uniform
         tqs += 2 * (unsigned long long)nvalid;
         if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
         return;
     }
-    if (start) s.run_at[before] = b.a[0];
-    int su[2] = {0, 0}, sv[2] = {0, 0};
+    const int tl = (pk & 0xffff) + (start ? 0 : -1) + (pk >> 16) + (gap ? 1 : 0);   // id of t_L
+    if (start) s.run_at[tl] = b.a[0];
+    if (open_r) s.run_at[tl + 1] = b.a[0] + 1;     // t_R not shared with the next run
+    int su[4] = {0, 0, 0, 0}, sv[4] = {0, 0, 0, 0};
     unsigned ins = 0;
-    unsigned long long ku[2] = {0, 0}, kv[2] = {0, 0};
+    unsigned long long ku[4] = {0, 0, 0, 0}, kv[4] = {0, 0, 0, 0};
     if (valid) {
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
+        for (int j = 0; j < 4; ++j) {   // j = 2 * side + d
+            const unsigned long long tk = (unsigned long long)(tl + (j >> 1)) << 54;
             bool fresh;
-            ku[d] = ((unsigned long long)run << 54) | (b.a[1] + d);
-            su[d] = sh_insert(sh.ukey, ku[d], &fresh);
-            if (fresh) ins |= 1u << d;
-            kv[d] = ((unsigned long long)run << 54) | (b.a[2] + d);
-            sv[d] = sh_insert(sh.vkey, kv[d], &fresh);
-            if (fresh) ins |= 4u << d;
+            ku[j] = tk | (b.a[1] + (j & 1));
+            su[j] = sh_insert(sh.ukey, ku[j], &fresh);
+            if (fresh) ins |= 1u << j;
+            kv[j] = tk | (b.a[2] + (j & 1));
+            sv[j] = sh_insert(sh.vkey, kv[j], &fresh);
+            if (fresh) ins |= 16u << j;
         }
     }
     __syncthreads();
-    int tot;
     const int pack =
-        block_scan_1sync<BS>(__popc(ins & 3u) | (__popc(ins >> 2) << 16), &tot, s.scan_b);
+        block_scan_1sync<BS>(__popc(ins & 15u) | (__popc(ins >> 4) << 16), &tot, s.scan_b);
     const int NU = tot & 0xffff, NV = tot >> 16;
     const bool share = NU <= SH_ENTRY_CAP && NV <= SH_ENTRY_CAP;   // block-uniform
     if (share) {
         int iu = pack & 0xffff, iv = pack >> 16;
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
-            if (ins & (1u << d)) { sh.uid[su[d]] = iu; sh.ukey_by_id[iu] = ku[d]; ++iu; }
-            if (ins & (4u << d)) { sh.vid[sv[d]] = iv; sh.vkey_by_id[iv] = kv[d]; ++iv; }
+        for (int j = 0; j < 4; ++j) {
+            if (ins & (1u << j)) { sh.uid[su[j]] = iu; sh.ukey_by_id[iu] = ku[j]; ++iu; }
+            if (ins & (16u << j)) { sh.vid[sv[j]] = iv; sh.vkey_by_id[iv] = kv[j]; ++iv; }
         }
-        tqs += 2 * (unsigned long long)nrun;
-        for (int task = tid; task < 2 * nrun; task += BS)
-            t_quantities<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[task >> 1] + (task & 1), k[0])),
-                               sh.tq[task]);
+        tqs += (unsigned long long)ntv;
+        for (int task = tid; task < ntv; task += BS)
+            t_quantities<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[task], k[0])), sh.tq[task]);
     }
     __syncthreads();
     if (!share) {
@@ -807,42 +817,40 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
         return;
     }
-    atasks += 2 * (unsigned long long)NU;
-    btasks += 2 * (unsigned long long)NV;
+    atasks += (unsigned long long)NU;
+    btasks += (unsigned long long)NV;
     shared_evals += (unsigned long long)nvalid;
-    for (int task = tid; task < 2 * (NU + NV); task += BS) {
-        const int side = task & 1;
-        int e = task >> 1;
-        if (e < NU) {
-            const unsigned long long key = sh.ukey_by_id[e];
+    for (int task = tid; task < NU + NV; task += BS) {
+        if (task < NU) {
+            const unsigned long long key = sh.ukey_by_id[task];
             const double u = dyadic(key & SH_VAL_MASK, k[1]);
-            const double *T = sh.tq[2 * (int)(key >> 54) + side];
+            const double *T = sh.tq[(int)(key >> 54)];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                sh.a[e][side][c] = KIND == CCD_KIND_VF ? dsub(T[c], dmul(u, T[3 + c]))
-                                                       : dadd(T[c], dmul(u, T[3 + c]));
+                sh.a[task][c] = KIND == CCD_KIND_VF ? dsub(T[c], dmul(u, T[3 + c]))
+                                                    : dadd(T[c], dmul(u, T[3 + c]));
         } else {
-            e -= NU;
+            const int e = task - NU;
             const unsigned long long key = sh.vkey_by_id[e];
             const double v = dyadic(key & SH_VAL_MASK, k[2]);
-            const double *T = sh.tq[2 * (int)(key >> 54) + side];
+            const double *T = sh.tq[(int)(key >> 54)];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                sh.b[e][side][c] = KIND == CCD_KIND_VF ? dmul(v, T[6 + c])
-                                                       : dadd(T[6 + c], dmul(v, T[9 + c]));
+                sh.b[e][c] = KIND == CCD_KIND_VF ? dmul(v, T[6 + c])
+                                                 : dadd(T[6 + c], dmul(v, T[9 + c]));
         }
     }
     __syncthreads();
     if (valid) {
-        const int u0 = sh.uid[su[0]], u1 = sh.uid[su[1]];
-        const int v0 = sh.vid[sv[0]], v1 = sh.vid[sv[1]];
         long long km[3], kM[3];
 #pragma unroll
-        for (int side = 0; side < 2; ++side)
+        for (int side = 0; side < 2; ++side) {
+            const int u0 = sh.uid[su[2 * side]], u1 = sh.uid[su[2 * side + 1]];
+            const int v0 = sh.vid[sv[2 * side]], v1 = sh.vid[sv[2 * side + 1]];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double al = sh.a[u0][side][c], ar = sh.a[u1][side][c];
-                const double bl = sh.b[v0][side][c], br = sh.b[v1][side][c];
+                const double al = sh.a[u0][c], ar = sh.a[u1][c];
+                const double bl = sh.b[v0][c], br = sh.b[v1][c];
                 const long long k0 = dkey(dsub(al, bl)), k1 = dkey(dsub(al, br));
                 const long long k2 = dkey(dsub(ar, bl)), k3 = dkey(dsub(ar, br));
                 const long long lo = min(min(k0, k1), min(k2, k3));
@@ -850,6 +858,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
                 if (side == 0) { km[c] = lo; kM[c] = hi; }
                 else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
             }
+        }
         box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
     }
 }
