@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--ref-sample", type=int, default=4_000)
+    ap.add_argument("--max-itr", type=int, default=10**6,
+                    help="check limit m_I of the simulation-mixed run (profiling cases only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deep-slots", type=int, default=None,
@@ -225,7 +227,7 @@ def run_native(args):
     batches = wl.batches
     verts = [ccd.to_soa(b.verts, dev) for b in batches]
     host = [torch.from_numpy(np.ascontiguousarray(b.verts.T)).pin_memory() for b in batches]
-    ws = [ccd.workspace(b.n, 10**6, dev, deep_slots=args.deep_slots) for b in batches]
+    ws = [ccd.workspace(b.n, args.max_itr, dev, deep_slots=args.deep_slots) for b in batches]
     res = [ccd.Result(torch.empty(b.n, dtype=torch.uint8, device=dev),
                       torch.empty(b.n, dtype=torch.float64, device=dev),
                       torch.empty(b.n, dtype=torch.float64, device=dev),
@@ -237,7 +239,7 @@ def run_native(args):
             if stage_sets is not None:
                 ccd.set_stage_events(stage_sets[j])
             err = ccd.err_from_bounds(b.kind, verts[j])
-            ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=10**6, ws=ws[j], out=res[j])
+            ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=args.max_itr, ws=ws[j], out=res[j])
         ccd.set_stage_events(None)
 
     # FP64 pipe peak, measured in this run (fma.rn.f64 chains, all SMs)
@@ -333,7 +335,7 @@ def run_native(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
-                   "delta": 1e-6, "max_itr": 10**6, "ms": 0.0,
+                   "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0,
                    "l2": "inputs 192 MB per step > 129 MB L2; no flush",
                    "parallelism": f"{world} GPU(s), queries sharded, no collective"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -349,9 +351,9 @@ def run_native(args):
         "counters": {("VF" if b.kind == 0 else "EE"): counters[j] for j, b in enumerate(batches)},
         "checks": {"mean": float(checks.mean()), "p50": float(np.percentile(checks, 50)),
                    "p99": float(np.percentile(checks, 99)), "max": int(checks.max()),
-                   "early_termination_pct": float(100.0 * np.mean(checks >= 10**6))},
+                   "early_termination_pct": float(100.0 * np.mean(checks >= args.max_itr))},
         "false_negatives": fn, "toi_after_truth": toi_bad,
-        "gpu_launches": args.steps * len(batches) * 7,
+        "gpu_launches": args.steps * len(batches) * 8,
         "clocks": clk,
     }
 
@@ -367,7 +369,7 @@ def run_native(args):
             for j, b in enumerate(batches):
                 verts[j].copy_(host[j], non_blocking=True)
                 err = ccd.err_from_bounds(b.kind, verts[j])
-                ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=10**6, ws=ws[j],
+                ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=args.max_itr, ws=ws[j],
                           out=dres[j])
                 out_host[j][0].copy_(dres[j].collides, non_blocking=True)
                 out_host[j][1].copy_(dres[j].toi, non_blocking=True)

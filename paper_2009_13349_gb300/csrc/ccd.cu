@@ -83,7 +83,8 @@ struct Header {
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
 struct Layout {
-    size_t off_surv, off_mid, off_over, off_kappa, off_pool, off_small, off_deep, total;
+    size_t off_surv, off_mid, off_over, off_level, off_dlist, off_kappa, off_pool, off_small,
+        off_deep, total;
     int nb_pool, nb_small, nb_deep;
     long long cap_small, cap_deep;
 };
@@ -547,6 +548,8 @@ struct Params {
     int *surv;       // level-0 survivors           -> pooled solver
     int *mid;        // pooled solver hand-offs     -> one-warp solver
     int *over;       // one-warp solver hand-offs   -> deep solver
+    unsigned char *over_level;   // level at which each hand-off outgrew its slot
+    int *deep_list;  // `over` ordered by that level, shallowest first
     double *kappa;
 };
 
@@ -891,7 +894,8 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
 
 template <int KIND, int BS>
 __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur, Box *nxt,
-                            long long cap, bool fallback, Smem<BS> &s, double *tq)
+                            long long cap, bool fallback, Smem<BS> &s, double *tq,
+                            int &hand_level)
 {
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
@@ -1107,6 +1111,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
         if (nchild > cap) {
             if (!fallback) {
                 if (tid == 0) count_done(p, false, 0, evals, tqs);
+                hand_level = k[0] + k[1] + k[2];
                 return false;
             }
             // answered as at the check limit: conservative, flagged
@@ -1128,12 +1133,14 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 }
 
 // Persistent: blocks take queries from `list` (length *count, work counter
-// *head); a query whose frontier outgrows `cap` goes to out_list (one-warp
-// tier only; the deep tier answers it through the capacity fallback).
+// *head); a query whose frontier outgrows `cap` goes to out_list, with the
+// level it reached in out_level when that is not null (one-warp tier only;
+// the deep tier answers it through the capacity fallback).
 template <int KIND, int BS>
 __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
     solve_kernel(Params p, int deep, Box *slots, long long cap, const int *list,
-                 const int *count, int *head, int *out_list, int *out_count)
+                 const int *count, int *head, int *out_list, unsigned char *out_level,
+                 int *out_count)
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
@@ -1147,11 +1154,51 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
         __syncthreads();
         if (idx >= *(volatile const int *)count) return;
         const long long qi = list[idx];
-        const bool done =
-            solve_query<KIND, BS>(p, qp_single(p, qi), qi, cur, nxt, cap, deep != 0, s, tq);
-        if (!done && threadIdx.x == 0) out_list[atomicAdd(out_count, 1)] = (int)qi;
+        int level = 0;
+        const bool done = solve_query<KIND, BS>(p, qp_single(p, qi), qi, cur, nxt, cap, deep != 0,
+                                                s, tq, level);
+        if (!done && threadIdx.x == 0) {
+            const int j = atomicAdd(out_count, 1);
+            out_list[j] = (int)qi;
+            if (out_level) out_level[j] = (unsigned char)level;
+        }
         __syncthreads();
     }
+}
+
+// Deep-tier schedule.  The level at which a query's frontier outgrew the
+// one-warp slot predicts its remaining work closely (the shallower, the
+// wider the colliding region and the more boxes it takes), so the deep
+// solver takes them shallowest first (longest-first scheduling shortens the
+// tail where blocks run out of queries).  One block, counting sort over the
+// levels (at most 3 * KMAX < 256); the order within a level is arbitrary.
+// Results do not depend on the order.
+__global__ void __launch_bounds__(1024)
+    order_by_level_kernel(const int *in, const unsigned char *level, const int *count, int *out)
+{
+    __shared__ int hist[256];
+    const int n = *count;
+    const int tid = threadIdx.x;
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&hist[level[i]], 1);
+    __syncthreads();
+    if (tid < 32) {   // exclusive scan of the 256 bins, 8 per lane
+        int v[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { v[j] = hist[tid * 8 + j]; sum += v[j]; }
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (tid >= o) inc += y;
+        }
+        int run = inc - sum;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { hist[tid * 8 + j] = run; run += v[j]; }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) out[atomicAdd(&hist[level[i]], 1)] = in[i];
 }
 
 // ---- pooled solver (small frontiers, many queries per warp) -------------------
@@ -1444,7 +1491,7 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
     extern __shared__ double tq[];   // [2 * BS][TWidth<EE>::W]: sized for either kind
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
-    const int *list = deep ? p.over : p.surv;
+    const int *list = deep ? p.deep_list : p.surv;
     const int *count = deep ? &p.hdr->overflow : &p.hdr->survivors;
     int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
     for (;;) {
@@ -1456,11 +1503,16 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
         const long long qi = list[idx];
         const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
         const QP q = qp_segment(sg);
+        int level = 0;
         const bool done =
             sg.kind == CCD_KIND_VF
-                ? solve_query<CCD_KIND_VF, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq)
-                : solve_query<CCD_KIND_EE, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq);
-        if (!done && threadIdx.x == 0) p.over[atomicAdd(&p.hdr->overflow, 1)] = (int)qi;
+                ? solve_query<CCD_KIND_VF, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq, level)
+                : solve_query<CCD_KIND_EE, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq, level);
+        if (!done && threadIdx.x == 0) {
+            const int j = atomicAdd(&p.hdr->overflow, 1);
+            p.over[j] = (int)qi;
+            p.over_level[j] = (unsigned char)level;
+        }
         __syncthreads();
     }
 }
@@ -1672,6 +1724,8 @@ Layout layout_fixed(long long n, int sms)
     L.off_surv = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_mid = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_over = off; off = align256(off + sizeof(int) * (size_t)n);
+    L.off_level = off; off = align256(off + (size_t)n);
+    L.off_dlist = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_kappa = off; off = align256(off + 3 * sizeof(double) * (size_t)n);
     L.nb_pool = sms * POOL_BLOCKS_PER_SM;
     L.off_pool = off;
@@ -1741,6 +1795,8 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     p.surv = (int *)(ws + L.off_surv);
     p.mid = (int *)(ws + L.off_mid);
     p.over = (int *)(ws + L.off_over);
+    p.over_level = (unsigned char *)(ws + L.off_level);
+    p.deep_list = (int *)(ws + L.off_dlist);
     p.kappa = (double *)(ws + L.off_kappa);
     Header *h = p.hdr;
 
@@ -1758,11 +1814,12 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
         return CCD_ERR_CUDA;
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
-        &h->overflow);
+        p.over_level, &h->overflow);
+    order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &h->overflow, p.deep_list);
     stage_mark(3, st);
     solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, tq_deep, st>>>(
-        p, 1, (Box *)(ws + L.off_deep), L.cap_deep, p.over, &h->overflow, &h->head_deep, nullptr,
-        nullptr);
+        p, 1, (Box *)(ws + L.off_deep), L.cap_deep, p.deep_list, &h->overflow, &h->head_deep,
+        nullptr, nullptr, nullptr);
     stage_mark(4, st);
     if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
     return CCD_OK;
@@ -1950,6 +2007,8 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
     size_t off = align256(sizeof(Header));
     off = align256(off + sizeof(int) * (size_t)n);          // survivors
     off = align256(off + sizeof(int) * (size_t)n);          // overflow
+    off = align256(off + (size_t)n);                        // overflow levels
+    off = align256(off + sizeof(int) * (size_t)n);          // deep list
     off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
     off = align256(off + sizeof(Box) * 2 * (size_t)T.small_cap * (size_t)(sms * T.small_blocks_per_sm));
     return off;
@@ -1968,6 +2027,7 @@ ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int ns
     stage_mark(2, st);   // no pooled stage in the multi-instance path
     solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
         p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
+    order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &p.hdr->overflow, p.deep_list);
     stage_mark(3, st);
     solve_kernel_seg<DT><<<nb_deep, DT, tq_deep, st>>>(p, segs, nseg, 1, (Box *)(ws + off_deep),
                                                        cap_deep);
@@ -2007,6 +2067,8 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     p.surv = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.mid = nullptr;
     p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.over_level = (unsigned char *)(ws + off); off = align256(off + (size_t)n);
+    p.deep_list = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
     const size_t off_small = off;
     const int nb_small = sms * T.small_blocks_per_sm;
@@ -2191,6 +2253,8 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     p.surv = (int *)(ws + STATIC_OFF_SURV);
     p.mid = nullptr;
     p.over = (int *)(ws + STATIC_OFF_OVER);
+    p.over_level = nullptr;   // no deep-tier ordering in the static-scratch path
+    p.deep_list = nullptr;
     p.kappa = (double *)(ws + STATIC_OFF_KAPPA);
     Header *h = p.hdr;
 
@@ -2204,9 +2268,9 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
         return CCD_ERR_CUDA;
     solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<STATIC_SMALL_BLOCKS, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP, p.surv, &h->survivors,
-        &h->head_small, p.over, &h->overflow);
+        &h->head_small, p.over, nullptr, &h->overflow);
     solve_kernel<CCD_KIND_VF, DEEP_THREADS><<<STATIC_DEEP_SLOTS, DEEP_THREADS, tq_deep, st>>>(
         p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP, p.over, &h->overflow, &h->head_deep,
-        nullptr, nullptr);
+        nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
