@@ -87,6 +87,11 @@ def _lib():
             lib.oracle_ccd_batch_t.restype = ctypes.c_longlong
             lib.oracle_kappa_t.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
             lib.oracle_kappa_t.restype = None
+            lib.oracle_linf_distance.argtypes = [ctypes.c_int, dp]
+            lib.oracle_linf_distance.restype = ctypes.c_double
+            lib.oracle_linf_distance_batch.argtypes = [ctypes.c_int, dp, ctypes.c_longlong, dp,
+                                                       ctypes.c_int]
+            lib.oracle_linf_distance_batch.restype = None
             _LIB = lib
         return _LIB
 
@@ -181,3 +186,17 @@ def ccd_batch(kind: int, verts, err, ms: float = 0.0, delta: float = 1e-6,
     if fails:
         raise MemoryError(f"oracle queue allocation failed for {fails} queries")
     return col, toi, tol, chk
+
+
+def linf_distance(kind: int, query) -> float:
+    """L-infinity distance between the primitives at t = 0 (Sec. 5.1 norm)."""
+    q = _as_queries(query)[0]
+    return _lib().oracle_linf_distance(kind, _dptr(q))
+
+
+def linf_distance_batch(kind: int, verts, nthreads: int = 1) -> np.ndarray:
+    """linf_distance of n queries (n x 24)."""
+    v = _as_queries(verts)
+    out = np.zeros(v.shape[0])
+    _lib().oracle_linf_distance_batch(kind, _dptr(v), v.shape[0], _dptr(out), int(nthreads))
+    return out

@@ -39,6 +39,7 @@
 #include <string.h>
 
 #define ORACLE_LITERAL_DROP 1
+#define ORACLE_VF 0
 
 /* Sec. 3, "Multivariate CCD Formulation": linear trajectory
  * p(t) = (1-t) p^0 + t p^1, evaluated as p^0 + (p^1 - p^0) t. */
@@ -387,4 +388,130 @@ long long oracle_ccd_batch(int kind, const double *verts, long long n,
 {
     return oracle_ccd_batch_t(kind, verts, n, err, err_stride, ms, delta, max_itr, 1.0,
                               flags, collides, toi, out_tol, checks, nthreads);
+}
+
+/* ---- L-infinity distance at t = 0 (Sec. 5.1 norm; Algorithm 4's d_i) -------
+ *
+ * f(u,v) = F(0,u,v) = A + u B + v C with, per axis c, one rounded
+ * subtraction of t = 0 coordinates:
+ *   VF: A = p - v1, B = v1 - v2, C = v1 - v3   (F = (q - u e1) - v e2)
+ *   EE: A = p1 - p3, B = p2 - p1, C = p3 - p4  (F = (p1 + u d1) - (p3 + v d2))
+ * The distance is min over the domain (VF: u, v >= 0, u + v <= 1; EE:
+ * [0,1]^2) of g(u,v) = max_c |(A_c + u B_c) + v C_c|.  That is a linear
+ * program in (u, v, s) whose minimum lies at a vertex of its feasible set,
+ * and every vertex is one of:
+ *   - a corner of the domain;
+ *   - a point of a domain edge where two of the six lines +-f_c cross
+ *     (f_c = 0, or f_c1 = +-f_c2);
+ *   - an interior point where f_c1 = f_c2 = 0, or s1 f_1 = s2 f_2 = s3 f_3
+ *     for a sign pattern s (four patterns up to a global sign).
+ * g is evaluated at each such candidate that lies in the domain and the
+ * minimum is returned.  Candidate points carry rounding, so the result is
+ * the distance up to the rounding of these few operations. */
+static double linf_g(const double A[3], const double B[3], const double C[3], double u, double v)
+{
+    double g = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double f = fabs((A[c] + u * B[c]) + v * C[c]);
+        if (f > g) g = f;
+    }
+    return g;
+}
+
+static int in_domain(int kind, double u, double v)
+{
+    if (!(u >= 0.0 && v >= 0.0)) return 0;
+    if (kind == ORACLE_VF) return u + v <= 1.0;
+    return u <= 1.0 && v <= 1.0;
+}
+
+double oracle_linf_distance(int kind, const double *q)
+{
+    double A[3], B[3], C[3];
+    for (int c = 0; c < 3; ++c) {
+        const double x0 = q[c], x1 = q[3 + c], x2 = q[6 + c], x3 = q[9 + c];
+        if (kind == ORACLE_VF) {
+            A[c] = x0 - x1; B[c] = x1 - x2; C[c] = x1 - x3;
+        } else {
+            A[c] = x0 - x2; B[c] = x1 - x0; C[c] = x2 - x3;
+        }
+    }
+    double best = INFINITY, g;
+    /* domain corners */
+    const double cu[4] = {0.0, 1.0, 0.0, 1.0}, cv[4] = {0.0, 0.0, 1.0, 1.0};
+    const int ncorner = kind == ORACLE_VF ? 3 : 4;
+    for (int i = 0; i < ncorner; ++i) {
+        g = linf_g(A, B, C, cu[i], cv[i]);
+        if (g < best) best = g;
+    }
+    /* domain edges (u, v) = P + tau D, tau in [0, 1]:
+     * VF: v = 0, u = 0, u + v = 1;  EE: v = 0, u = 0, u = 1, v = 1 */
+    const double vf_P[3][2] = {{0, 0}, {0, 0}, {1, 0}}, vf_D[3][2] = {{1, 0}, {0, 1}, {-1, 1}};
+    const double ee_P[4][2] = {{0, 0}, {0, 0}, {1, 0}, {0, 1}};
+    const double ee_D[4][2] = {{1, 0}, {0, 1}, {0, 1}, {1, 0}};
+    const int nedge = kind == ORACLE_VF ? 3 : 4;
+    for (int e = 0; e < nedge; ++e) {
+        const double pu = kind == ORACLE_VF ? vf_P[e][0] : ee_P[e][0];
+        const double pv = kind == ORACLE_VF ? vf_P[e][1] : ee_P[e][1];
+        const double du = kind == ORACLE_VF ? vf_D[e][0] : ee_D[e][0];
+        const double dv = kind == ORACLE_VF ? vf_D[e][1] : ee_D[e][1];
+        double al[3], be[3];
+        for (int c = 0; c < 3; ++c) {
+            al[c] = (A[c] + pu * B[c]) + pv * C[c];
+            be[c] = du * B[c] + dv * C[c];
+        }
+        double tau[9];
+        int nt = 0;
+        for (int c = 0; c < 3; ++c)
+            if (be[c] != 0.0) tau[nt++] = -al[c] / be[c];
+        for (int c1 = 0; c1 < 3; ++c1)
+            for (int c2 = c1 + 1; c2 < 3; ++c2)
+                for (int s = 0; s < 2; ++s) {
+                    const double sg = s ? -1.0 : 1.0;
+                    const double den = be[c1] - sg * be[c2];
+                    if (den != 0.0) tau[nt++] = (sg * al[c2] - al[c1]) / den;
+                }
+        for (int i = 0; i < nt; ++i) {
+            const double t = tau[i];
+            if (!(t >= 0.0 && t <= 1.0)) continue;
+            g = linf_g(A, B, C, pu + t * du, pv + t * dv);
+            if (g < best) best = g;
+        }
+    }
+    /* interior: two axes zero */
+    for (int c1 = 0; c1 < 3; ++c1)
+        for (int c2 = c1 + 1; c2 < 3; ++c2) {
+            const double det = B[c1] * C[c2] - C[c1] * B[c2];
+            if (det == 0.0) continue;
+            const double u = (C[c1] * A[c2] - A[c1] * C[c2]) / det;
+            const double v = (A[c1] * B[c2] - B[c1] * A[c2]) / det;
+            if (!in_domain(kind, u, v)) continue;
+            g = linf_g(A, B, C, u, v);
+            if (g < best) best = g;
+        }
+    /* interior: s1 f_1 = s2 f_2 = s3 f_3 */
+    const double sgn[4][3] = {{1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+    for (int k = 0; k < 4; ++k) {
+        const double s1 = sgn[k][0], s2 = sgn[k][1], s3 = sgn[k][2];
+        const double a11 = s1 * B[0] - s2 * B[1], a12 = s1 * C[0] - s2 * C[1];
+        const double b1 = s2 * A[1] - s1 * A[0];
+        const double a21 = s2 * B[1] - s3 * B[2], a22 = s2 * C[1] - s3 * C[2];
+        const double b2 = s3 * A[2] - s2 * A[1];
+        const double det = a11 * a22 - a12 * a21;
+        if (det == 0.0) continue;
+        const double u = (b1 * a22 - a12 * b2) / det;
+        const double v = (a11 * b2 - b1 * a21) / det;
+        if (!in_domain(kind, u, v)) continue;
+        g = linf_g(A, B, C, u, v);
+        if (g < best) best = g;
+    }
+    return best;
+}
+
+void oracle_linf_distance_batch(int kind, const double *verts, long long n, double *out,
+                                int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (long long i = 0; i < n; ++i) out[i] = oracle_linf_distance(kind, verts + 24 * i);
 }

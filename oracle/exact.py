@@ -12,6 +12,8 @@ forms, independently of the floating-point operation order in
   exact arithmetic, an emptied queue certifies that F has no root in the
   domain (B_F is an inclusion function, Proposition 1).
 * ``coplanarity_cubic`` -- f(t) = <n(t), q(t)> of Eq. (univariate).
+* ``linf_distance`` -- min over the domain of ||F(0,u,v)||_inf (Sec. 5.1
+  norm), the exact optimum of that linear program by vertex enumeration.
 """
 from __future__ import annotations
 
@@ -169,3 +171,62 @@ def coplanarity_cubic(kind: int, query) -> list[Fr]:
         f = padd(f, pmul(n[c], qq[c]))
     f = f + [Fr(0)] * (4 - len(f))
     return f[:4]
+
+
+def linf_distance(kind: int, query) -> Fr:
+    """Exact min over the domain (VF triangle, EE unit square) of
+    max_c |F_c(0,u,v)|, with F affine in (u, v) at t = 0.  The linear program
+    min s s.t. -s <= F_c(u,v) <= s, (u,v) in the domain has its optimum at a
+    vertex of its feasible set: a domain corner, a point of a domain edge
+    where two of the lines +-F_c cross, or an interior point where three of
+    them meet (two axes zero, or s1 F_1 = s2 F_2 = s3 F_3).  Every such point
+    is computed exactly and the exact objective is minimised over them."""
+    q = query if isinstance(query[0], Fr) else to_fr(query)
+    zero, one = Fr(0), Fr(1)
+
+    def f(u, v):
+        return F(kind, q, zero, u, v)
+
+    def g(u, v):
+        return max(abs(x) for x in f(u, v))
+
+    def inside(u, v):
+        if u < 0 or v < 0:
+            return False
+        return u + v <= 1 if kind == VF else (u <= 1 and v <= 1)
+
+    A = f(zero, zero)
+    Bu = [f(one, zero)[c] - A[c] for c in range(3)]
+    Cv = [f(zero, one)[c] - A[c] for c in range(3)]
+    pts = [(zero, zero), (one, zero), (zero, one)] + ([(one, one)] if kind == EE else [])
+    edges = ([((0, 0), (1, 0)), ((0, 0), (0, 1)), ((1, 0), (-1, 1))] if kind == VF else
+             [((0, 0), (1, 0)), ((0, 0), (0, 1)), ((1, 0), (0, 1)), ((0, 1), (1, 0))])
+    for (pu, pv), (du, dv) in edges:
+        al = [A[c] + pu * Bu[c] + pv * Cv[c] for c in range(3)]
+        be = [du * Bu[c] + dv * Cv[c] for c in range(3)]
+        taus = [-al[c] / be[c] for c in range(3) if be[c] != 0]
+        for c1 in range(3):
+            for c2 in range(c1 + 1, 3):
+                for sg in (1, -1):
+                    den = be[c1] - sg * be[c2]
+                    if den != 0:
+                        taus.append((sg * al[c2] - al[c1]) / den)
+        pts += [(pu + t * du, pv + t * dv) for t in taus if 0 <= t <= 1]
+    rows = []
+    for c1 in range(3):
+        for c2 in range(c1 + 1, 3):
+            rows.append(((Bu[c1], Cv[c1], -A[c1]), (Bu[c2], Cv[c2], -A[c2])))
+    for s1, s2, s3 in ((1, 1, 1), (1, 1, -1), (1, -1, 1), (-1, 1, 1)):
+        s = (s1, s2, s3)
+        rows.append(((s[0] * Bu[0] - s[1] * Bu[1], s[0] * Cv[0] - s[1] * Cv[1],
+                      s[1] * A[1] - s[0] * A[0]),
+                     (s[1] * Bu[1] - s[2] * Bu[2], s[1] * Cv[1] - s[2] * Cv[2],
+                      s[2] * A[2] - s[1] * A[1])))
+    for (a11, a12, b1), (a21, a22, b2) in rows:
+        det = a11 * a22 - a12 * a21
+        if det != 0:
+            u = (b1 * a22 - a12 * b2) / det
+            v = (a11 * b2 - b1 * a21) / det
+            if inside(u, v):
+                pts.append((u, v))
+    return min(g(u, v) for u, v in pts if inside(u, v))
