@@ -241,6 +241,88 @@ ccd_status ccd_group_reduce(const double *toi, const double *out_tol, int64_t n,
                             double *alpha, double *tol, void *stream);
 
 /*
+ * L-infinity distance between the two primitives of each query at t = 0 (the
+ * norm of minimum separation, Sec. 5.1): min over the domain (VF triangle
+ * u, v >= 0, u + v <= 1; EE unit square) of max_c |F_c(0, u, v)|.  This is
+ * Algorithm 4's distance d_i (Sec. 6, "Line Search") of a candidate.
+ *
+ * Fixed operation sequence (round to nearest, no contraction):
+ *   A, B, C per axis, one subtraction each of t = 0 coordinates:
+ *     VF: A = p - v1, B = v1 - v2, C = v1 - v3;  EE: A = p1 - p3,
+ *     B = p2 - p1, C = p3 - p4;
+ *   g(u, v) = max_c |(A_c + u B_c) + v C_c|;
+ *   the result is the minimum of g over the linear program's candidate
+ *   vertices that lie in the domain: the domain corners; on each domain edge
+ *   (u, v) = (pu + tau du, pv + tau dv) with alpha_c = (A_c + pu B_c) +
+ *   pv C_c and beta_c = du B_c + dv C_c, tau = -alpha_c / beta_c and tau =
+ *   (s alpha_c2 - alpha_c1) / (beta_c1 - s beta_c2) for c1 < c2, s = +-1,
+ *   where 0 <= tau <= 1; in the interior the solutions (u, v) = (b1 a22 -
+ *   a12 b2, a11 b2 - b1 a21) / (a11 a22 - a12 a21) of f_c1 = f_c2 = 0 and of
+ *   s1 f_1 = s2 f_2 = s3 f_3 for the sign patterns (+,+,+), (+,+,-),
+ *   (+,-,+), (-,+,+).
+ * The rounding of these few operations is the error rho_i that Algorithm 4
+ * adds to its inequality.
+ *
+ * verts: SoA as for ccd_multi_batch, segs: DEVICE segment table (kind and
+ * group of each query).  dist: n doubles or NULL; group_min: ngroups doubles,
+ * the minimum over each group's queries (+inf for an empty group).  Queries
+ * of segments with group >= ngroups only get dist.  Device pointers.
+ */
+ccd_status ccd_linf_distance(const double *verts, int64_t n, const ccd_segment *segs,
+                             int32_t nseg, int32_t ngroups, double *dist, double *group_min,
+                             void *stream);
+
+/*
+ * Algorithm 4's CCD step for one line search (Sec. 6): given the candidate
+ * set C (n_vf vertex-face queries followed by n_ee edge-edge queries in one
+ * SoA array, x1 = x0 + dx already applied), computes
+ *   d_i     = min over C of the L-infinity distance at t = 0;
+ *   eps_i   = max over kinds and axes of the scene's Eq. msccd-error;
+ *   d       = min(p d_i, delta), or max(p d_i, delta) with cap_max = 1 (the
+ *             printed formula; the text caps d at delta);
+ *   find p:   while (d_i - d) > ((delta + eps_i) + rho) fails and a smaller p
+ *             could satisfy it: p <- p / 2, d recomputed;
+ *   a pass:   SolveMSCCD with ms = d, tolerance delta, check limit max_itr on
+ *             the interval [0, alpha] for every candidate (all with the alpha
+ *             of the pass's start); alpha <- min(alpha, min toi), delta_i <-
+ *             max(delta, max out_tol);
+ *   validate: done if (d_i - d) > ((delta_i + eps_i) + rho); otherwise
+ *             delta <- delta_i and back to find p, for at most max_passes
+ *             passes (or until alpha = 0).
+ * The backtracking on the energy that follows in Algorithm 4 belongs to the
+ * caller.  Inputs: p in (0, 1), delta > 0, rho >= 0 (the paper uses 1e-9),
+ * max_itr >= 1, max_passes >= 1.  Outputs: alpha (the step bound in
+ * [0, 1]), p_out (the validated p), d, d_i, eps_i, delta_i, passes and
+ * validated (1 when the inequality holds at return).  Synchronizes `stream`
+ * after each pass (the loop decides on the host).  verts is a device
+ * pointer; io lives in host memory; workspace (device) is at least
+ * ccd_line_search_workspace_bytes(n_vf + n_ee, max_itr).  Returns
+ * CCD_ERR_CAPACITY when a pass fell back on a frontier (outputs stay
+ * conservative), otherwise as for ccd_multi_batch.
+ */
+typedef struct {
+    double p;            /* in  */
+    double delta;        /* in  */
+    double rho;          /* in  */
+    int64_t max_itr;     /* in  */
+    int32_t max_passes;  /* in  */
+    int32_t cap_max;     /* in: 0 = min(p d_i, delta), 1 = max(p d_i, delta) */
+    double alpha;        /* out */
+    double p_out;        /* out */
+    double d;            /* out */
+    double d_i;          /* out */
+    double eps_i;        /* out */
+    double delta_i;      /* out */
+    int32_t passes;      /* out */
+    int32_t validated;   /* out */
+} ccd_line_search_io;
+
+size_t ccd_line_search_workspace_bytes(int64_t n, int64_t max_itr);
+ccd_status ccd_line_search(const double *verts, int64_t n_vf, int64_t n_ee,
+                           ccd_line_search_io *io, void *workspace, size_t ws_bytes,
+                           void *stream);
+
+/*
  * Layout helper: copies n queries from an array of structures aos[n][24]
  * (query-major, the same 24-value order) into columns [0, n) of a structure
  * of arrays with plane stride ld >= n: soa[k * ld + i] = aos[i * 24 + k].

@@ -66,6 +66,12 @@ def lib():
         L.ccd_group_reduce.argtypes = [dp, dp, i64, vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
                                        vp]
         L.ccd_group_reduce.restype = ctypes.c_int
+        L.ccd_linf_distance.argtypes = [dp, i64, vp, ctypes.c_int32, ctypes.c_int32, dp, dp, vp]
+        L.ccd_linf_distance.restype = ctypes.c_int
+        L.ccd_line_search_workspace_bytes.argtypes = [i64, i64]
+        L.ccd_line_search_workspace_bytes.restype = sz
+        L.ccd_line_search.argtypes = [dp, i64, i64, ctypes.POINTER(LineSearchIO), vp, sz, vp]
+        L.ccd_line_search.restype = ctypes.c_int
         L.ccd_aos_to_soa.argtypes = [dp, i64, dp, i64, vp]
         L.ccd_aos_to_soa.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
@@ -324,6 +330,62 @@ def group_reduce(res: Result, seg_dev: torch.Tensor, ngroups: int, stream=None):
                                   int(ngroups), _ptr(alpha), _ptr(tol), _stream(stream)),
            "ccd_group_reduce")
     return alpha, tol
+
+
+def linf_distance(verts: torch.Tensor, seg_dev: torch.Tensor, ngroups: int = 1,
+                  per_query: bool = False, stream=None):
+    """L-infinity distance at t = 0 of every query (ccd_linf_distance):
+    (group_min, dist or None), device tensors."""
+    _require_cuda(verts, "verts", torch.float64)
+    n = verts.shape[1]
+    nseg = seg_dev.numel() // SEGMENT_DTYPE.itemsize
+    gmin = torch.empty(ngroups, dtype=torch.float64, device=verts.device)
+    dist = torch.empty(n, dtype=torch.float64, device=verts.device) if per_query else None
+    _check(lib().ccd_linf_distance(_ptr(verts), n, _ptr(seg_dev), nseg, int(ngroups),
+                                   _ptr(dist) if dist is not None else None, _ptr(gmin),
+                                   _stream(stream)), "ccd_linf_distance")
+    return gmin, dist
+
+
+class LineSearchIO(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double), ("delta", ctypes.c_double), ("rho", ctypes.c_double),
+                ("max_itr", ctypes.c_int64), ("max_passes", ctypes.c_int32),
+                ("cap_max", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("p_out", ctypes.c_double), ("d", ctypes.c_double), ("d_i", ctypes.c_double),
+                ("eps_i", ctypes.c_double), ("delta_i", ctypes.c_double),
+                ("passes", ctypes.c_int32), ("validated", ctypes.c_int32)]
+
+
+def line_search_workspace(n: int, max_itr: int, device=None) -> torch.Tensor:
+    nb = lib().ccd_line_search_workspace_bytes(int(n), int(max_itr))
+    if nb == 0:
+        raise CCDError(-4, "ccd_line_search_workspace_bytes")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def line_search(verts: torch.Tensor, n_vf: int, n_ee: int, p: float, delta: float,
+                max_itr: int = 10**6, rho: float = 1e-9, max_passes: int = 16,
+                cap: str = "min", ws: torch.Tensor | None = None, stream=None) -> dict:
+    """Algorithm 4's CCD step over one candidate set (ccd_line_search): the
+    first n_vf columns of verts are vertex-face queries, the next n_ee
+    edge-edge queries.  Returns alpha, p, d, d_i, eps_i, delta_i, passes and
+    validated."""
+    _require_cuda(verts, "verts", torch.float64)
+    if cap not in ("min", "max"):
+        raise ValueError("cap is 'min' or 'max'")
+    if verts.shape[1] != n_vf + n_ee:
+        raise ValueError("verts has n_vf + n_ee columns")
+    if ws is None:
+        ws = line_search_workspace(n_vf + n_ee, max_itr, verts.device)
+    io = LineSearchIO(p=float(p), delta=float(delta), rho=float(rho), max_itr=int(max_itr),
+                      max_passes=int(max_passes), cap_max=1 if cap == "max" else 0)
+    code = lib().ccd_line_search(_ptr(verts), int(n_vf), int(n_ee), ctypes.byref(io), _ptr(ws),
+                                 ws.numel(), _stream(stream))
+    if code not in (0, -5):
+        raise CCDError(code, "ccd_line_search")
+    return {"alpha": io.alpha, "p": io.p_out, "d": io.d, "d_i": io.d_i, "eps_i": io.eps_i,
+            "delta_i": io.delta_i, "passes": io.passes, "validated": bool(io.validated),
+            "status": code}
 
 
 def aos_to_soa(aos: torch.Tensor, soa: torch.Tensor, col: int = 0, stream=None) -> None:

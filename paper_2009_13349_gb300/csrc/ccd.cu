@@ -1566,6 +1566,171 @@ __global__ void group_reduce_kernel(const double *__restrict__ toi,
     }
 }
 
+// ---- L-infinity distance at t = 0 (Sec. 5.1 norm; Algorithm 4's d_i) ---------
+//
+// f(u,v) = F(0,u,v) = A + u B + v C, each component one rounded subtraction
+// of t = 0 coordinates (VF: A = p - v1, B = v1 - v2, C = v1 - v3; EE:
+// A = p1 - p3, B = p2 - p1, C = p3 - p4).  The distance min over the domain
+// of g = max_c |(A_c + u B_c) + v C_c| is a linear program in (u, v, s); its
+// optimum is at a vertex, so g is taken at every candidate vertex (domain
+// corners; points of a domain edge where two of the lines +-f_c cross;
+// interior points where two axes vanish or three signed lines meet) and the
+// smallest value is the answer.  The operation sequence of every candidate is
+// fixed (include/ccd.h states it), so the result is reproducible bit for bit.
+struct LinfQ {
+    double A[3], B[3], C[3];
+    int vf;
+};
+
+__device__ __forceinline__ double linf_at(const LinfQ &L, double u, double v)
+{
+    double g = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double f = fabs(dadd(dadd(L.A[c], dmul(u, L.B[c])), dmul(v, L.C[c])));
+        g = f > g ? f : g;
+    }
+    return g;
+}
+
+__device__ __forceinline__ bool linf_inside(const LinfQ &L, double u, double v)
+{
+    if (!(u >= 0.0) || !(v >= 0.0)) return false;
+    return L.vf ? dadd(u, v) <= 1.0 : (u <= 1.0 && v <= 1.0);
+}
+
+// the candidate (u, v) = (b1 a22 - a12 b2, a11 b2 - b1 a21) / det of a 2x2 system
+__device__ __forceinline__ void linf_solve2(const LinfQ &L, double a11, double a12, double b1,
+                                            double a21, double a22, double b2, double &best)
+{
+    const double det = dsub(dmul(a11, a22), dmul(a12, a21));
+    if (det == 0.0) return;
+    const double u = __ddiv_rn(dsub(dmul(b1, a22), dmul(a12, b2)), det);
+    const double v = __ddiv_rn(dsub(dmul(a11, b2), dmul(b1, a21)), det);
+    if (linf_inside(L, u, v)) best = fmin(best, linf_at(L, u, v));
+}
+
+__device__ double linf_distance(const double *__restrict__ verts, long long n, long long i,
+                                int kind)
+{
+    LinfQ L;
+    L.vf = kind == CCD_KIND_VF;
+    double x[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[j][c] = verts[(size_t)(3 * j + c) * n + i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (L.vf) {
+            L.A[c] = dsub(x[0][c], x[1][c]);
+            L.B[c] = dsub(x[1][c], x[2][c]);
+            L.C[c] = dsub(x[1][c], x[3][c]);
+        } else {
+            L.A[c] = dsub(x[0][c], x[2][c]);
+            L.B[c] = dsub(x[1][c], x[0][c]);
+            L.C[c] = dsub(x[2][c], x[3][c]);
+        }
+    }
+    double best = __longlong_as_double(0x7ff0000000000000LL);
+    // corners (0,0), (1,0), (0,1) and, for EE, (1,1)
+    best = fmin(best, linf_at(L, 0.0, 0.0));
+    best = fmin(best, linf_at(L, 1.0, 0.0));
+    best = fmin(best, linf_at(L, 0.0, 1.0));
+    if (!L.vf) best = fmin(best, linf_at(L, 1.0, 1.0));
+    // edges (u, v) = (pu, pv) + tau (du, dv), tau in [0, 1]:
+    // VF v = 0, u = 0, u + v = 1;  EE v = 0, u = 0, u = 1, v = 1
+    const int nedge = L.vf ? 3 : 4;
+    for (int e = 0; e < nedge; ++e) {
+        double pu, pv, du, dv;
+        if (e == 0) { pu = 0.0; pv = 0.0; du = 1.0; dv = 0.0; }
+        else if (e == 1) { pu = 0.0; pv = 0.0; du = 0.0; dv = 1.0; }
+        else if (e == 2) {
+            if (L.vf) { pu = 1.0; pv = 0.0; du = -1.0; dv = 1.0; }
+            else { pu = 1.0; pv = 0.0; du = 0.0; dv = 1.0; }
+        } else { pu = 0.0; pv = 1.0; du = 1.0; dv = 0.0; }
+        double al[3], be[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            al[c] = dadd(dadd(L.A[c], dmul(pu, L.B[c])), dmul(pv, L.C[c]));
+            be[c] = dadd(dmul(du, L.B[c]), dmul(dv, L.C[c]));
+        }
+        // 3 zero crossings, then f_c1 = +-f_c2 for the 3 axis pairs
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double num, den;
+            if (k < 3) {
+                num = -al[k];
+                den = be[k];
+            } else {
+                const int pair = (k - 3) >> 1;               // (0,1), (0,2), (1,2)
+                const int c1 = pair == 2 ? 1 : 0, c2 = pair == 0 ? 1 : 2;
+                const double sg = ((k - 3) & 1) ? -1.0 : 1.0;
+                num = dsub(dmul(sg, al[c2]), al[c1]);
+                den = dsub(be[c1], dmul(sg, be[c2]));
+            }
+            if (den == 0.0) continue;
+            const double t = __ddiv_rn(num, den);
+            if (!(t >= 0.0 && t <= 1.0)) continue;
+            best = fmin(best, linf_at(L, dadd(pu, dmul(t, du)), dadd(pv, dmul(t, dv))));
+        }
+    }
+    // interior: two axes zero
+    linf_solve2(L, L.B[0], L.C[0], -L.A[0], L.B[1], L.C[1], -L.A[1], best);
+    linf_solve2(L, L.B[0], L.C[0], -L.A[0], L.B[2], L.C[2], -L.A[2], best);
+    linf_solve2(L, L.B[1], L.C[1], -L.A[1], L.B[2], L.C[2], -L.A[2], best);
+    // interior: s1 f_1 = s2 f_2 = s3 f_3, patterns (+,+,+), (+,+,-), (+,-,+), (-,+,+)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double s1 = k == 3 ? -1.0 : 1.0, s2 = k == 2 ? -1.0 : 1.0, s3 = k == 1 ? -1.0 : 1.0;
+        linf_solve2(L, dsub(dmul(s1, L.B[0]), dmul(s2, L.B[1])),
+                    dsub(dmul(s1, L.C[0]), dmul(s2, L.C[1])),
+                    dsub(dmul(s2, L.A[1]), dmul(s1, L.A[0])),
+                    dsub(dmul(s2, L.B[1]), dmul(s3, L.B[2])),
+                    dsub(dmul(s2, L.C[1]), dmul(s3, L.C[2])),
+                    dsub(dmul(s3, L.A[2]), dmul(s2, L.A[1])), best);
+    }
+    return best;
+}
+
+__global__ void linf_group_init_kernel(double *gmin, int ngroups)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ngroups) gmin[g] = __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// per query (optional) and per segment group (minimum, through the bit
+// patterns: distances are >= +0, so their bits order like their values)
+__global__ void linf_distance_kernel(const double *__restrict__ verts, long long n,
+                                     const ccd_segment *segs, int nseg, int ngroups,
+                                     double *dist, double *gmin)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        int grp = -1;
+        unsigned long long bits = 0x7ff0000000000000ull;
+        if (valid) {
+            const ccd_segment sg = segs[find_segment(segs, nseg, i)];
+            const double d = linf_distance(verts, n, i, sg.kind);
+            if (dist) dist[i] = d;
+            bits = (unsigned long long)__double_as_longlong(d);
+            grp = sg.group < ngroups ? sg.group : -1;
+        }
+        const int g0 = __shfl_sync(FULL, grp, 0);
+        if (__all_sync(FULL, grp == g0)) {
+            for (int o = 16; o; o >>= 1)
+                bits = min(bits, (unsigned long long)__shfl_xor_sync(FULL, bits, o));
+            if (lane == 0 && g0 >= 0) atomicMin((unsigned long long *)&gmin[g0], bits);
+        } else if (grp >= 0) {
+            atomicMin((unsigned long long *)&gmin[grp], bits);
+        }
+    }
+}
+
 // per-segment eps from the segment's own points
 __global__ void seg_err_init_kernel(ccd_segment *segs, int nseg)
 {
@@ -2130,6 +2295,162 @@ ccd_status ccd_group_reduce(const double *toi, const double *out_tol, int64_t n,
                                                              ngroups, alpha, tol);
     }
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+ccd_status ccd_linf_distance(const double *verts, int64_t n, const ccd_segment *segs,
+                             int32_t nseg, int32_t ngroups, double *dist, double *group_min,
+                             void *stream)
+{
+    if (n < 0 || n >= 0x7fffffffLL || ngroups < 1 || !group_min ||
+        (n > 0 && (!verts || !segs || nseg < 1)))
+        return CCD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    linf_group_init_kernel<<<(ngroups + 255) / 256, 256, 0, st>>>(group_min, ngroups);
+    if (n > 0) {
+        const int sms = device_sms();
+        if (sms <= 0) return CCD_ERR_CUDA;
+        long long blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms) blocks = 8LL * sms;
+        linf_distance_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, n, segs, nseg, ngroups,
+                                                              dist, group_min);
+    }
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+// ---- Algorithm 4's CCD step (host driver over the device kernels) -------------
+
+namespace {
+
+constexpr size_t LS_OFF_SEGS = 0;      // 2 segments (160 B)
+constexpr size_t LS_OFF_RED = 256;     // alpha, tol, d_i
+constexpr size_t LS_OFF_OUT = 512;     // per-query outputs, then the batch workspace
+
+size_t ls_out_bytes(long long n)
+{
+    return align256((size_t)n) + 2 * align256(sizeof(double) * (size_t)n);
+}
+
+double ls_cap(double x, double delta, int cap_max)
+{
+    if (cap_max) return x > delta ? x : delta;
+    return x < delta ? x : delta;
+}
+
+}  // namespace
+
+size_t ccd_line_search_workspace_bytes(int64_t n, int64_t max_itr)
+{
+    const size_t m = ccd_multi_workspace_bytes(n, max_itr, nullptr);
+    if (m == 0) return 0;
+    return LS_OFF_OUT + ls_out_bytes(n) + m;
+}
+
+ccd_status ccd_line_search(const double *verts, int64_t n_vf, int64_t n_ee,
+                           ccd_line_search_io *io, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!io || n_vf < 0 || n_ee < 0 || n_vf + n_ee >= 0x7fffffffLL) return CCD_ERR_ARG;
+    const long long n = n_vf + n_ee;
+    if (!(io->p > 0.0 && io->p < 1.0) || !(io->delta > 0.0) || !(io->rho >= 0.0) ||
+        io->max_itr < 1 || io->max_passes < 1 || (n > 0 && !verts))
+        return CCD_ERR_ARG;
+    const size_t need = ccd_line_search_workspace_bytes(n, io->max_itr);
+    if (need == 0) return CCD_ERR_CUDA;
+    if (!workspace || ws_bytes < need) return CCD_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    ccd_segment *dsegs = (ccd_segment *)(ws + LS_OFF_SEGS);
+    double *red = (double *)(ws + LS_OFF_RED);
+    uint8_t *collides = (uint8_t *)(ws + LS_OFF_OUT);
+    double *toi = (double *)(ws + LS_OFF_OUT + align256((size_t)n));
+    double *out_tol = toi + align256(sizeof(double) * (size_t)n) / sizeof(double);
+    char *mws = ws + LS_OFF_OUT + ls_out_bytes(n);
+    const size_t mws_bytes = ws_bytes - (LS_OFF_OUT + ls_out_bytes(n));
+
+    // two segments of one candidate set; ms > 0 selects Eq. msccd-error
+    ccd_segment segs[2];
+    for (int k = 0; k < 2; ++k) {
+        segs[k].offset = k == 0 ? 0 : n_vf;
+        segs[k].count = k == 0 ? n_vf : n_ee;
+        segs[k].kind = k == 0 ? CCD_KIND_VF : CCD_KIND_EE;
+        segs[k].group = 0;
+        segs[k].err[0] = segs[k].err[1] = segs[k].err[2] = 0.0;
+        segs[k].ms = 1.0;
+        segs[k].delta = io->delta;
+        segs[k].max_itr = io->max_itr;
+        segs[k].t_max = 1.0;
+    }
+    const double inf = __builtin_inf();
+    double d_i = inf, eps_i = 0.0;
+    if (n > 0) {
+        if (cudaMemcpyAsync(dsegs, segs, sizeof(segs), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return CCD_ERR_CUDA;
+        ccd_status r = ccd_segments_err_from_bounds(verts, n, dsegs, 2, st);
+        if (r != CCD_OK) return r;
+        r = ccd_linf_distance(verts, n, dsegs, 2, 1, nullptr, red + 2, st);
+        if (r != CCD_OK) return r;
+        if (cudaMemcpyAsync(segs, dsegs, sizeof(segs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&d_i, red + 2, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CCD_ERR_CUDA;
+        for (int k = 0; k < 2; ++k)
+            if (segs[k].count > 0)
+                for (int c = 0; c < 3; ++c) eps_i = segs[k].err[c] > eps_i ? segs[k].err[c] : eps_i;
+    }
+
+    double p = io->p, alpha = 1.0, delta_cur = io->delta, delta_i = io->delta;
+    double d = ls_cap(p * d_i, delta_cur, io->cap_max);
+    bool validated = (d_i - d) > ((delta_cur + eps_i) + io->rho);
+    int passes = 0;
+    ccd_status result = CCD_OK;
+    while (n > 0) {
+        // find p: halve while the inequality fails and a smaller p could satisfy it
+        while (!((d_i - d) > ((delta_cur + eps_i) + io->rho))) {
+            const double lim = io->cap_max ? delta_cur : 0.0;
+            if (!((d_i - lim) > ((delta_cur + eps_i) + io->rho)) || p == 0.0) break;
+            p = p / 2.0;
+            d = ls_cap(p * d_i, delta_cur, io->cap_max);
+        }
+        if (alpha == 0.0) break;   // no time interval left
+        // one MSCCD pass on [0, alpha] (SolveMSCCD with ms = d)
+        for (int k = 0; k < 2; ++k) {
+            segs[k].ms = d;
+            segs[k].delta = delta_cur;
+            segs[k].t_max = alpha;
+        }
+        if (cudaMemcpyAsync(dsegs, segs, sizeof(segs), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return CCD_ERR_CUDA;
+        ccd_status r = ccd_multi_batch(verts, n, dsegs, 2, io->max_itr, collides, toi, out_tol,
+                                       nullptr, nullptr, mws, mws_bytes, stream);
+        if (r != CCD_OK) return r;
+        r = ccd_group_reduce(toi, out_tol, n, dsegs, 2, 1, red, red + 1, stream);
+        if (r != CCD_OK) return r;
+        double got[2];
+        int32_t status = 0;
+        if (cudaMemcpyAsync(got, red, sizeof(got), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&status, &((const Header *)mws)->status, sizeof(status),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CCD_ERR_CUDA;
+        if (status == CCD_ERR_ARG) return CCD_ERR_ARG;
+        if (status != CCD_OK) result = (ccd_status)status;   // capacity: still conservative
+        delta_i = delta_cur;
+        alpha = got[0] < alpha ? got[0] : alpha;
+        delta_i = got[1] > delta_i ? got[1] : delta_i;
+        passes += 1;
+        // validate after
+        validated = (d_i - d) > ((delta_i + eps_i) + io->rho);
+        if (validated || passes >= io->max_passes) break;
+        delta_cur = delta_i;
+    }
+    io->alpha = alpha;
+    io->p_out = p;
+    io->d = d;
+    io->d_i = d_i;
+    io->eps_i = eps_i;
+    io->delta_i = delta_i;
+    io->passes = passes;
+    io->validated = validated ? 1 : 0;
+    return result;
 }
 
 ccd_status ccd_aos_to_soa(const double *aos, int64_t n, double *soa, int64_t ld, void *stream)

@@ -488,3 +488,57 @@ def request_stream(clients: int = 16, duration_s: float = 2.0, rate_hz: float = 
 
 def request_batch(req) -> Batch:
     return unit_cube(req["kind"], req["size"], req["seed"])
+
+
+def line_search_scene(n: int = 1_000_000, seed: int = 5, h: float = 1.0 / 64,
+                      approach=(0.0, 2.0), g: float = 2.0**-30) -> Workload:
+    """Candidate set of one line-search step (Sec. 6, Algorithm 4), VF:EE 1:1.
+
+    Each pair is a flat local configuration of mesh size h, tilted by up to
+    30 degrees and placed in the unit cube: VF a triangle and a point above
+    its interior, EE an edge and a crossing edge above it, separated by a gap
+    along the normal that is log-uniform in [10^-2, 1] h.  The update dx
+    moves the upper primitive toward the lower one by s times the gap,
+    s ~ U(approach) (s > 1 closes the gap within the full step), plus
+    N(0, (1e-3 h)^2) on every coordinate.  Coordinates are on a 2^-30 grid."""
+    rng = np.random.default_rng(seed)
+    batches = []
+    for kind, m in ((VF, n // 2), (EE, n - n // 2)):
+        # rotation: spin about z, then tilt about x by up to 30 degrees
+        tx = rng.uniform(-np.pi / 6, np.pi / 6, m)
+        sp = rng.uniform(0, 2 * np.pi, m)
+        cx, sx, cz, sz = np.cos(tx), np.sin(tx), np.cos(sp), np.sin(sp)
+        R = np.zeros((m, 3, 3))
+        R[:, 0, 0], R[:, 0, 1] = cz, -sz
+        R[:, 1, 0], R[:, 1, 1], R[:, 1, 2] = cx * sz, cx * cz, -sx
+        R[:, 2, 0], R[:, 2, 1], R[:, 2, 2] = sx * sz, sx * cz, cx
+        c = rng.uniform(0.1, 0.9, (m, 3))
+        gap = h * 10.0 ** rng.uniform(-2.0, 0.0, m)
+        if kind == VF:
+            local = np.zeros((m, 4, 3))
+            local[:, 2, :2] = [h, 0.0]
+            local[:, 3, :2] = [0.0, h]
+            local[:, 1:, :2] += rng.uniform(-0.2, 0.2, (m, 3, 2)) * h
+            u = rng.uniform(0.1, 0.45, m)
+            v = rng.uniform(0.1, 0.45, m)
+            local[:, 0] = ((1 - u - v)[:, None] * local[:, 1] + u[:, None] * local[:, 2]
+                           + v[:, None] * local[:, 3])
+            local[:, 0, 2] = gap
+            mover = [0]
+        else:
+            local = np.zeros((m, 4, 3))
+            local[:, 0, 0], local[:, 1, 0] = -0.5 * h, 0.5 * h
+            ang = rng.uniform(np.pi / 6, 5 * np.pi / 6, m)
+            local[:, 2, 0], local[:, 2, 1] = -0.5 * h * np.cos(ang), -0.5 * h * np.sin(ang)
+            local[:, 3, 0], local[:, 3, 1] = 0.5 * h * np.cos(ang), 0.5 * h * np.sin(ang)
+            local[:, 2:, :2] += rng.uniform(-0.1, 0.1, (m, 2, 2)) * h
+            local[:, 2:, 2] = gap[:, None]
+            mover = [2, 3]
+        L1 = local.copy()
+        L1[:, mover, 2] -= (rng.uniform(approach[0], approach[1], m) * gap)[:, None]
+        P0 = q(np.einsum("nij,nkj->nki", R, local) + c[:, None], g)
+        P1 = q(np.einsum("nij,nkj->nki", R, L1) + c[:, None] + rng.normal(0, 1e-3 * h, L1.shape),
+               g)
+        batches.append(Batch(kind, _pack(P0, P1), np.full(m, -1, np.int8),
+                             np.full(m, np.nan)))
+    return Workload("line-search", batches, {"seed": seed, "h": h, "approach": approach})
