@@ -60,13 +60,15 @@ def parse():
     ap.add_argument("--deep-slots", type=int, default=None,
                     help="cap the deep-solver slots (smaller workspace, e.g. for profiling)")
     ap.add_argument("--workload", default="simulation-mixed",
-                    choices=["simulation-mixed", "multi-instance", "served"])
+                    choices=["simulation-mixed", "multi-instance", "served", "line-search"])
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multi-instance/served: fraction of the full query count")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of arrivals")
     ap.add_argument("--req-scale", type=float, default=0.1,
                     help="served: request sizes are log-uniform in [100, 500k] times this")
     ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--compare-printed-cap", action="store_true",
+                    help="line-search: also time d = max(p d_i, delta) (about a minute a step)")
     return ap.parse_args()
 
 
@@ -611,6 +613,65 @@ def run_served(args):
                    "tuning": tuning},
         "loads": results}))
 
+def run_line_search(args):
+    """One line-search step (Algorithm 4's CCD part) over a candidate set of
+    args.n pairs: distance, p validation, MSCCD passes, reduction.  Also the
+    printed cap d = max(p d_i, delta), and the oracle's step on the same set
+    (all host cores) for a check and a CPU rate."""
+    import torch
+    import oracle
+    from oracle.linesearch import line_search_ccd
+    from paper_2009_13349_gb300 import ccd, workloads as W
+    dev = torch.device("cuda", 0)
+    wl = W.line_search_scene(n=args.n, seed=args.seed if args.seed != 1 else 5)
+    vf, ee = wl.batches[0].verts, wl.batches[1].verts
+    verts = ccd.to_soa(np.concatenate([vf, ee]), dev)
+    ws = ccd.line_search_workspace(len(vf) + len(ee), 10**6, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(cap, steps, warmup):
+        out = None
+        for _ in range(warmup):
+            ccd.line_search(verts, len(vf), len(ee), p=0.5, delta=1e-6, cap=cap, ws=ws)
+        ms = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            out = ccd.line_search(verts, len(vf), len(ee), p=0.5, delta=1e-6, cap=cap, ws=ws)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return out, ms
+
+    clocks = Clocks(0)
+    clocks.start()
+    res, ms = timed("min", args.steps, args.warmup)
+    clk = clocks.stop()
+    res_max, ms_max = (timed("max", 1, 0) if args.compare_printed_cap else (None, None))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o = line_search_ccd(vf, ee, p=0.5, delta=1e-6, nthreads=cores)
+    cpu_s = time.perf_counter() - t0
+    keys = ("alpha", "p", "d", "d_i", "eps_i", "delta_i", "passes", "validated")
+    n = len(vf) + len(ee)
+    step_ms = float(np.median(ms))
+    print(json.dumps({
+        "metric": "line-search step (Algorithm 4 CCD part): candidates/s", "value": n / (step_ms * 1e-3),
+        "unit": "candidates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"line-search scene {n} candidates (VF:EE 1:1), seed 5",
+                   "p": 0.5, "delta": 1e-6, "rho": 1e-9, "max_itr": 10**6, "cap": "min"},
+        "step": {k: res[k] for k in keys},
+        "printed_cap_max": ({"ms_per_step": float(np.median(ms_max)),
+                             "step": {k: res_max[k] for k in keys}}
+                            if res_max is not None else None),
+        "identical_to_oracle": all(res[k] == o[k] for k in keys),
+        "cpu_baseline": {"value": n / cpu_s, "unit": "candidates/s", "cores": cores,
+                         "kind": "oracle", "sample": "the whole candidate set, one step"},
+        "clocks": clk}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -619,6 +680,8 @@ def main():
         run_multi_instance(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "line-search":
+        run_line_search(args)
     else:
         run_native(args)
 

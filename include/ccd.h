@@ -190,12 +190,17 @@ typedef struct {
  *  deep_slots           deep-solver blocks / frontier slots (two per SM)
  *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
  *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
+ *  pool_cap             boxes per level a query may reach in the pooled
+ *                       solver before the one-warp solver takes it over,
+ *                       32..4096 (64); the pooled slots take
+ *                       72 * pool_cap bytes each, 256 slots per SM
  */
 typedef struct {
     int32_t deep_threads;
     int32_t deep_slots;
     int32_t small_blocks_per_sm;
     int32_t small_cap;
+    int32_t pool_cap;
 } ccd_tuning;
 
 /* Workspace bytes for ccd_multi_batch (tuning may be NULL for defaults). */

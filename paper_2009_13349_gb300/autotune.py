@@ -13,6 +13,7 @@ Tunables (see include/ccd.h):
                        solved at once (0 = one per SM)
   small_blocks_per_sm  one-warp solver blocks per SM (its queue width)
   small_cap            frontier depth of a one-warp solver slot in boxes
+  pool_cap             boxes per level a query may reach in the pooled solver
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ import os
 import time
 from typing import Callable, Iterable
 
-FIELDS = ("deep_threads", "deep_slots", "small_blocks_per_sm", "small_cap")
+FIELDS = ("deep_threads", "deep_slots", "small_blocks_per_sm", "small_cap", "pool_cap")
 
 
 def candidates(sms: int) -> list[dict]:
@@ -29,8 +30,9 @@ def candidates(sms: int) -> list[dict]:
     for dt, slots in ((256, 2 * sms), (512, sms), (256, sms)):
         for sb in (8, 16):
             for cap in (256, 1024):
-                out.append({"deep_threads": dt, "deep_slots": slots,
-                            "small_blocks_per_sm": sb, "small_cap": cap})
+                for pc in (64, 1024):
+                    out.append({"deep_threads": dt, "deep_slots": slots,
+                                "small_blocks_per_sm": sb, "small_cap": cap, "pool_cap": pc})
     return out
 
 
@@ -42,6 +44,8 @@ def validate(t: dict) -> dict:
         raise ValueError("bad slot or block count")
     if t["small_cap"] and t["small_cap"] < 64:
         raise ValueError("small_cap must be >= 64")
+    if t["pool_cap"] and not 32 <= t["pool_cap"] <= 4096:
+        raise ValueError("pool_cap must be in 32..4096")
     return t
 
 

@@ -232,7 +232,8 @@ assert SEGMENT_DTYPE.itemsize == 80
 class Tuning(ctypes.Structure):
     """ccd_tuning: launch shapes only (results never depend on them)."""
     _fields_ = [("deep_threads", ctypes.c_int32), ("deep_slots", ctypes.c_int32),
-                ("small_blocks_per_sm", ctypes.c_int32), ("small_cap", ctypes.c_int32)]
+                ("small_blocks_per_sm", ctypes.c_int32), ("small_cap", ctypes.c_int32),
+                ("pool_cap", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -47,7 +47,8 @@ constexpr int SMALL_THREADS = 32;     // one warp per query
 constexpr int SMALL_BLOCKS_PER_SM = 16;
 constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
-constexpr int POOL_CAP = 64;          // ... boxes per level per query ...
+constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
+constexpr int POOL_CAP_MAX = 4096;
 constexpr int POOL_BLOCKS_PER_SM = 8; // ... and one-warp blocks per SM
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM
@@ -78,7 +79,8 @@ struct Header {
     unsigned long long evals_shared_deep;  // deep box evaluations from shared partials
     unsigned long long checks_pool;   // sum of n over queries finished by the pooled solver
     unsigned long long evals_pool;    // box evaluations executed by the pooled solver
-    int pad[34];
+    int head_pool_ee;                 // work counter of the EE pooled solver (segmented batches)
+    int pad[33];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -1201,6 +1203,34 @@ __global__ void __launch_bounds__(1024)
     for (int i = tid; i < n; i += blockDim.x) out[atomicAdd(&hist[level[i]], 1)] = in[i];
 }
 
+// ---- segment tables ------------------------------------------------------------
+
+static_assert(sizeof(ccd_segment) == 80, "ccd_segment layout");
+
+// Segment of query i: the last segment whose offset is <= i.
+__device__ __forceinline__ int find_segment(const ccd_segment *segs, int nseg, long long i)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].offset <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
+{
+    QP q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q.eps[c] = sg.err[c];
+    q.ms = sg.ms;
+    q.delta = sg.delta;
+    q.max_itr = sg.max_itr;
+    q.t_max = sg.t_max;
+    return q;
+}
+
 // ---- pooled solver (small frontiers, many queries per warp) -------------------
 //
 // An FP64 warp-instruction costs the same for 1 or 32 active lanes, and most
@@ -1212,7 +1242,7 @@ __global__ void __launch_bounds__(1024)
 // its boxes in Q order: first colliding box, check limit, termination,
 // children appended in Q order (u/v splits: left then right; t splits: the
 // right children of a run of equal t_L wait in a pending list flushed when
-// the run ends).  A level with more than POOL_CAP children hands the query
+// the run ends).  A level with more children than the slot capacity hands the query
 // to the one-warp solver, which restarts it.
 struct PoolSlot {
     long long qi, size, pos, n_before;
@@ -1230,6 +1260,10 @@ struct PoolShared {
     Box box[32];
     double w[32];
     int hit[32], term[32], lane_slot[32], lane_off[32];
+    // distinct t values of an iteration (at most 32 runs + 31 gaps + 1)
+    double tq[64][12];
+    unsigned long long tv_a[64];
+    int tv_slot[64];
 };
 
 __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[3])
@@ -1244,15 +1278,20 @@ __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[
     S.can_split = S.k[S.sd] < KMAX;
 }
 
+// Queries come from `list` (length *count, work counter *head).  With a
+// segment table (segs != nullptr) each query takes its tolerances from its
+// segment and queries of the other kind are skipped (one launch per kind).
 template <int KIND>
-__global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
+__global__ void __launch_bounds__(32)
+    pool_kernel(Params p, Box *mem, int cap, const int *list, const int *count_p, int *head,
+                const ccd_segment *segs, int nseg)
 {
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ PoolShared sh;
     const int lane = threadIdx.x;
     PoolSlot &S = sh.st[lane];                     // the slot this lane owns
     Box *const mine = mem + ((size_t)blockIdx.x * POOL_SLOTS + lane) * 3 * (size_t)cap;
-    const int count = *(volatile const int *)&p.hdr->survivors;
+    const int count = *(volatile const int *)count_p;
     bool drained = false;
     unsigned long long evals = 0, checks_done = 0;
     int rot = 0;
@@ -1266,14 +1305,24 @@ __global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
         if (want) {
             const int leader = __ffs(want) - 1;
             int base = 0;
-            if (lane == leader) base = atomicAdd(&p.hdr->head_pool, __popc(want));
+            if (lane == leader) base = atomicAdd(head, __popc(want));
             base = __shfl_sync(FULL, base, leader);
             if (empty && !drained) {
                 const int idx = base + __popc(want & ((1u << lane) - 1u));
+                long long qi = -1;
+                bool mine_kind = true;
                 if (idx < count) {
-                    const long long qi = p.surv[idx];
+                    qi = list[idx];
+                    if (segs) {
+                        const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
+                        mine_kind = sg.kind == KIND;
+                        if (mine_kind) sh.qp[lane] = qp_segment(sg);
+                    } else {
+                        sh.qp[lane] = qp_single(p, qi);
+                    }
+                }
+                if (idx < count && mine_kind) {
                     load_query(p.verts, p.n, qi, sh.Q[lane]);
-                    sh.qp[lane] = qp_single(p, qi);
                     make_thresholds(sh.qp[lane].eps, sh.qp[lane].delta, sh.TH[lane]);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) sh.kap[lane][c] = p.kappa[3 * qi + c];
@@ -1287,14 +1336,14 @@ __global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
                     S.k[0] = S.k[1] = S.k[2] = 0;
                     pool_split_dim(S, sh.kap[lane]);
                     mine[0] = Box{{0ull, 0ull, 0ull}};
-                } else {
+                } else if (idx >= count) {
                     drained = true;
-                }
+                }   // a query of the other kind: this slot takes another next time
             }
         }
         __syncwarp();
         const bool active = S.qi >= 0;
-        if (!__any_sync(FULL, active)) break;
+        if (!__any_sync(FULL, active) && __all_sync(FULL, drained)) break;
 
         // 2. place the slots' next boxes in the lanes, rotating the priority
         const int rem = active ? (int)min(S.size - S.pos, 32LL) : 0;
@@ -1315,18 +1364,59 @@ __global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
         rot = (rot + 1) & 31;
         __syncwarp();
 
-        // 3. one box per lane
+        // 3. one box per lane.  A slot's boxes sit in consecutive lanes in Q
+        // order (ascending t_L), so the iteration's distinct t values get
+        // dense ids from one warp scan (t_L of a run: run + gaps so far; t_R:
+        // that id + 1; a slot change counts as a gap); their t-quantities are
+        // computed once, one task per (t value, axis), then every lane takes
+        // the corners of its box from them.
         const int nbox = min(total, 32);
+        const bool have = lane < nbox;
         BoxTest bt{false, false, 0.0};
         Box b = Box{{0ull, 0ull, 0ull}};
-        if (lane < nbox) {
-            const int so = sh.lane_slot[lane];
+        int so = 0;
+        if (have) {
+            so = sh.lane_slot[lane];
             const PoolSlot &T = sh.st[so];
             const Box *cur = mem + ((size_t)blockIdx.x * POOL_SLOTS + so) * 3 * (size_t)cap +
                              (T.buf ? cap : 0);
             b = cur[T.pos + sh.lane_off[lane]];
-            eval_box_private<KIND>(sh.Q[so], sh.qp[so], sh.TH[so], T.k, b, bt);
             evals += 1;
+        }
+        const unsigned long long at = b.a[0];
+        const int so_prev = __shfl_up_sync(FULL, so, 1), so_next = __shfl_down_sync(FULL, so, 1);
+        const unsigned long long at_prev = __shfl_up_sync(FULL, at, 1);
+        const unsigned long long at_next = __shfl_down_sync(FULL, at, 1);
+        const bool start = have && (lane == 0 || so_prev != so || at_prev != at);
+        const bool gap = start && lane > 0 && !(so_prev == so && at_prev + 1 == at);
+        const bool open_r = have && (lane + 1 >= nbox ||
+                                     !(so_next == so && (at_next == at || at_next == at + 1)));
+        int pk = (start ? 1 : 0) | ((gap ? 1 : 0) << 8);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, pk, o);
+            if (lane >= o) pk += y;
+        }
+        const int tl = (pk & 0xff) - 1 + (pk >> 8);
+        const int last = __shfl_sync(FULL, pk, 31);
+        const int ntv = nbox > 0 ? (last & 0xff) + (last >> 8) + 1 : 0;
+        if (start) { sh.tv_slot[tl] = so; sh.tv_a[tl] = at; }
+        if (open_r) { sh.tv_slot[tl + 1] = so; sh.tv_a[tl + 1] = at + 1; }
+        __syncwarp();
+        for (int task = lane; task < 3 * ntv; task += 32) {
+            const int tv = task / 3;
+            const int s2 = sh.tv_slot[tv];
+            t_quantities_axis<KIND>(sh.Q[s2], dmul(sh.qp[s2].t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
+                                    task - 3 * tv, sh.tq[tv]);
+        }
+        __syncwarp();
+        if (have) {
+            const PoolSlot &T = sh.st[so];
+            long long km[3], kM[3];
+            corners_keys<KIND>(sh.tq[tl], sh.tq[tl + 1], dyadic(b.a[1], T.k[1]),
+                               dyadic(b.a[1] + 1, T.k[1]), dyadic(b.a[2], T.k[2]),
+                               dyadic(b.a[2] + 1, T.k[2]), km, kM);
+            box_test_keys(km, kM, sh.TH[so], sh.qp[so].ms, bt.hit, bt.term, bt.w);
         }
         sh.box[lane] = b;
         sh.hit[lane] = bt.hit;
@@ -1428,33 +1518,6 @@ __global__ void __launch_bounds__(32) pool_kernel(Params p, Box *mem, int cap)
 
 // ---- multi-instance (segmented) kernels ---------------------------------------
 
-static_assert(sizeof(ccd_segment) == 80, "ccd_segment layout");
-static_assert(2 * 512 <= SH_SLOTS, "hash tables hold every key of a 512-box chunk");
-
-// Segment of query i: the last segment whose offset is <= i.
-__device__ __forceinline__ int find_segment(const ccd_segment *segs, int nseg, long long i)
-{
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].offset <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
-{
-    QP q;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) q.eps[c] = sg.err[c];
-    q.ms = sg.ms;
-    q.delta = sg.delta;
-    q.max_itr = sg.max_itr;
-    q.t_max = sg.t_max;
-    return q;
-}
-
 __global__ void seg_validate_kernel(const ccd_segment *segs, int nseg, long long n,
                                     long long max_itr_bound, Header *hdr)
 {
@@ -1491,8 +1554,8 @@ __global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
     extern __shared__ double tq[];   // [2 * BS][TWidth<EE>::W]: sized for either kind
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
-    const int *list = deep ? p.deep_list : p.surv;
-    const int *count = deep ? &p.hdr->overflow : &p.hdr->survivors;
+    const int *list = deep ? p.deep_list : p.mid;
+    const int *count = deep ? &p.hdr->overflow : &p.hdr->mid;
     int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(head, 1);
@@ -1969,7 +2032,8 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     stage_mark(0, st);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
-    pool_kernel<KIND><<<L.nb_pool, 32, 0, st>>>(p, (Box *)(ws + L.off_pool), POOL_CAP);
+    pool_kernel<KIND><<<L.nb_pool, 32, 0, st>>>(p, (Box *)(ws + L.off_pool), POOL_CAP, p.surv,
+                                                &h->survivors, &h->head_pool, nullptr, 0);
     stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
     const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
@@ -2146,22 +2210,23 @@ namespace {
 // ---- multi-instance host side ---------------------------------------------------
 
 struct Tuned {
-    int deep_threads, deep_slots, small_blocks_per_sm;
+    int deep_threads, deep_slots, small_blocks_per_sm, pool_cap;
     long long small_cap;
 };
 
 bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
 {
-    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, SMALL_CAP};
+    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
     if (t) {
         if (t->deep_threads) r.deep_threads = t->deep_threads;
         if (t->deep_slots) r.deep_slots = t->deep_slots;
         if (t->small_blocks_per_sm) r.small_blocks_per_sm = t->small_blocks_per_sm;
         if (t->small_cap) r.small_cap = t->small_cap;
+        if (t->pool_cap) r.pool_cap = t->pool_cap;
     }
     if (r.deep_threads != 256 && r.deep_threads != 512) return false;
     if (r.deep_slots < 1 || r.small_blocks_per_sm < 1 || r.small_blocks_per_sm > 32 ||
-        r.small_cap < 64)
+        r.small_cap < 64 || r.pool_cap < 32 || r.pool_cap > POOL_CAP_MAX)
         return false;
     *out = r;
     return true;
@@ -2171,25 +2236,37 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
 {
     size_t off = align256(sizeof(Header));
     off = align256(off + sizeof(int) * (size_t)n);          // survivors
+    off = align256(off + sizeof(int) * (size_t)n);          // pooled-solver hand-offs
     off = align256(off + sizeof(int) * (size_t)n);          // overflow
     off = align256(off + (size_t)n);                        // overflow levels
     off = align256(off + sizeof(int) * (size_t)n);          // deep list
     off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
+    off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
+                             (size_t)(sms * POOL_BLOCKS_PER_SM));   // pooled-solver slots
     off = align256(off + sizeof(Box) * 2 * (size_t)T.small_cap * (size_t)(sms * T.small_blocks_per_sm));
     return off;
 }
 
 template <int DT>
 ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int nseg, char *ws,
-                                size_t off_small, int nb_small, long long cap_small,
-                                size_t off_deep, int nb_deep, long long cap_deep, cudaStream_t st)
+                                Box *pool_mem, int nb_pool, int pool_cap, size_t off_small,
+                                int nb_small,
+                                long long cap_small, size_t off_deep, int nb_deep,
+                                long long cap_deep, cudaStream_t st)
 {
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
     const size_t tq_deep = sizeof(SharedUV);
     if (cudaFuncSetAttribute(solve_kernel_seg<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tq_deep) != cudaSuccess)
         return CCD_ERR_CUDA;
-    stage_mark(2, st);   // no pooled stage in the multi-instance path
+    // pooled stage: one launch per kind over the survivor list
+    pool_kernel<CCD_KIND_VF><<<nb_pool, 32, 0, st>>>(p, pool_mem, pool_cap, p.surv,
+                                                     &p.hdr->survivors, &p.hdr->head_pool, segs,
+                                                     nseg);
+    pool_kernel<CCD_KIND_EE><<<nb_pool, 32, 0, st>>>(p, pool_mem, pool_cap, p.surv,
+                                                     &p.hdr->survivors, &p.hdr->head_pool_ee,
+                                                     segs, nseg);
+    stage_mark(2, st);
     solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
         p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
     order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &p.hdr->overflow, p.deep_list);
@@ -2230,11 +2307,14 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     p.hdr = (Header *)ws;
     size_t off = align256(sizeof(Header));
     p.surv = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
-    p.mid = nullptr;
+    p.mid = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.over_level = (unsigned char *)(ws + off); off = align256(off + (size_t)n);
     p.deep_list = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
+    Box *pool_mem = (Box *)(ws + off);
+    off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
+                             (size_t)(sms * POOL_BLOCKS_PER_SM));
     const size_t off_small = off;
     const int nb_small = sms * T.small_blocks_per_sm;
 
@@ -2244,10 +2324,14 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
         p, segs, nseg);
     stage_mark(1, st);
     ccd_status r = T.deep_threads == 256
-                       ? launch_multi_solvers<256>(p, segs, nseg, ws, off_small, nb_small,
+                       ? launch_multi_solvers<256>(p, segs, nseg, ws, pool_mem,
+                                                   sms * POOL_BLOCKS_PER_SM, T.pool_cap,
+                                                   off_small, nb_small,
                                                    T.small_cap, fixed, (int)nb_deep,
                                                    deep_cap(max_itr_bound), st)
-                       : launch_multi_solvers<512>(p, segs, nseg, ws, off_small, nb_small,
+                       : launch_multi_solvers<512>(p, segs, nseg, ws, pool_mem,
+                                                   sms * POOL_BLOCKS_PER_SM, T.pool_cap,
+                                                   off_small, nb_small,
                                                    T.small_cap, fixed, (int)nb_deep,
                                                    deep_cap(max_itr_bound), st);
     if (r != CCD_OK) return r;
@@ -2338,9 +2422,13 @@ double ls_cap(double x, double delta, int cap_max)
 
 }  // namespace
 
+// MSCCD queries of a line search (ms = d <= delta) mostly bisect through many
+// small-to-medium levels: the pooled solver keeps them up to 1024 boxes a level.
+const ccd_tuning LS_TUNING = {0, 0, 0, 0, 1024};
+
 size_t ccd_line_search_workspace_bytes(int64_t n, int64_t max_itr)
 {
-    const size_t m = ccd_multi_workspace_bytes(n, max_itr, nullptr);
+    const size_t m = ccd_multi_workspace_bytes(n, max_itr, &LS_TUNING);
     if (m == 0) return 0;
     return LS_OFF_OUT + ls_out_bytes(n) + m;
 }
@@ -2420,7 +2508,7 @@ ccd_status ccd_line_search(const double *verts, int64_t n_vf, int64_t n_ee,
         if (cudaMemcpyAsync(dsegs, segs, sizeof(segs), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return CCD_ERR_CUDA;
         ccd_status r = ccd_multi_batch(verts, n, dsegs, 2, io->max_itr, collides, toi, out_tol,
-                                       nullptr, nullptr, mws, mws_bytes, stream);
+                                       nullptr, &LS_TUNING, mws, mws_bytes, stream);
         if (r != CCD_OK) return r;
         r = ccd_group_reduce(toi, out_tol, n, dsegs, 2, 1, red, red + 1, stream);
         if (r != CCD_OK) return r;
