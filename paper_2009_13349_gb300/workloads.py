@@ -542,3 +542,55 @@ def line_search_scene(n: int = 1_000_000, seed: int = 5, h: float = 1.0 / 64,
         batches.append(Batch(kind, _pack(P0, P1), np.full(m, -1, np.int8),
                              np.full(m, np.nan)))
     return Workload("line-search", batches, {"seed": seed, "h": h, "approach": approach})
+
+
+@dataclass
+class Mesh:
+    x0: np.ndarray       # (nv, 3) float64 positions at t0
+    x1: np.ndarray       # (nv, 3) float64 positions at t1
+    faces: np.ndarray    # (nf, 3) int32 vertex ids
+    edges: np.ndarray    # (ne, 2) int32 vertex ids, each edge once, a < b
+
+
+def _grid_sheet(nx, spacing, origin):
+    """nx x nx vertices on a square grid, two triangles per cell."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+    xy = np.stack([i.ravel(), j.ravel()], -1) * spacing + origin
+    idx = (i * nx + j)
+    a, b = idx[:-1, :-1].ravel(), idx[1:, :-1].ravel()
+    c, d = idx[:-1, 1:].ravel(), idx[1:, 1:].ravel()
+    faces = np.concatenate([np.stack([a, b, d], -1), np.stack([a, d, c], -1)])
+    return xy, faces
+
+
+def _mesh_edges(faces):
+    e = np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [0, 2]]])
+    e = np.sort(e, axis=1)
+    return np.unique(e, axis=0)
+
+
+def cloth_scene(nx: int = 256, seed: int = 6, gap: float = 0.25, fall: float = 0.5,
+                g: float = 2.0**-30) -> Mesh:
+    """Two cloth-like sheets of nx x nx vertices (spacing 1 / (nx - 1)) for
+    Algorithm 3's active set: sheet A lies near z = 0 with a small wave,
+    sheet B starts gap spacings above it, shifted by half a cell, and moves
+    down by fall + gap spacings with per-vertex jitter, so part of it passes
+    through A within the step.  Both sheets also carry their own
+    self-candidates (nearby primitives of one sheet)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (nx - 1)
+    xy_a, f_a = _grid_sheet(nx, h, np.array([0.0, 0.0]))
+    xy_b, f_b = _grid_sheet(nx, h, np.array([0.5 * h, 0.5 * h]))
+    wave = lambda xy: 0.5 * h * np.sin(2 * np.pi * xy[:, 0]) * np.sin(2 * np.pi * xy[:, 1])
+    za = wave(xy_a) + rng.normal(0, 0.02 * h, len(xy_a))
+    zb = wave(xy_b) + gap * h + rng.normal(0, 0.02 * h, len(xy_b))
+    A0 = np.concatenate([xy_a, za[:, None]], 1)
+    B0 = np.concatenate([xy_b, zb[:, None]], 1)
+    drop = (gap + fall) * h * (0.5 + 0.5 * np.sin(np.pi * xy_b[:, 0]))   # falls more mid-sheet
+    A1 = A0 + rng.normal(0, 0.02 * h, A0.shape)
+    B1 = B0 + rng.normal(0, 0.02 * h, B0.shape)
+    B1[:, 2] -= drop
+    x0 = q(np.concatenate([A0, B0]), g)
+    x1 = q(np.concatenate([A1, B1]), g)
+    faces = np.concatenate([f_a, f_b + len(xy_a)]).astype(np.int32)
+    return Mesh(x0, x1, faces, _mesh_edges(faces).astype(np.int32))
