@@ -328,6 +328,58 @@ ccd_status ccd_line_search(const double *verts, int64_t n_vf, int64_t n_ee,
                            void *stream);
 
 /*
+ * Active-set construction (Sec. 6, Algorithm 3) for a triangle mesh moving
+ * linearly from x0 to x1.  Mesh arrays are DEVICE arrays: x0, x1 are nv x 3
+ * doubles (vertex-major), faces nf x 3 and edges ne x 2 int32 vertex ids
+ * (each edge once).  Three steps:
+ *
+ * ccd_scene_eps: eps of the scene (Sec. 6 computes it from the bounds of all
+ *   the vertices of the simulation): gamma_c = max(1, max over every vertex
+ *   at both times of |x_c|), eps[3 k + c] = K_k ((gamma_c gamma_c) gamma_c)
+ *   with K of Eq. ccd-error for k = VF (0) and EE (1); eps is host memory.
+ *   workspace: at least 256 bytes of device memory.  Synchronizes `stream`.
+ *
+ * ccd_broad_phase: the candidate set C (the paper names the broad phase
+ *   only; this is its plain definition): every vertex-face pair (v, f), v not
+ *   a vertex of f, and every edge-edge pair (a, b), a < b, without a shared
+ *   vertex, whose swept boxes overlap.  A swept box is the per-axis min / max
+ *   of the primitive's vertices at both times, minus / plus margin; boxes
+ *   overlap when lo_1 <= hi_2 and lo_2 <= hi_1 on every axis.  With margin
+ *   >= max eps / 2 no pair that the CCD filter could report is missing (boxes
+ *   apart by more than eps on an axis keep |F_c| > eps there).  Output:
+ *   vf_pairs (cap_vf x 2: v, f) and ee_pairs (cap_ee x 2: a, b), each sorted
+ *   by (first, second); counts[0..1] (host) receive the numbers of pairs.
+ *   If a count exceeds its capacity the call returns CCD_ERR_CAPACITY with
+ *   the counts set and the lists undefined: call again with larger
+ *   capacities.  Uniform-grid method: cells of a power-of-two edge >= 1.01
+ *   times the largest swept box, CUB radix sorts.  Synchronizes `stream`.
+ *
+ * ccd_active_set: for every candidate, t <- CCD(x0 of c, x1 of c, delta,
+ *   max_itr) (Algorithm 2, ms = 0, eps of the scene); C_A = the candidates
+ *   with 0 <= t <= 1 (a reported collision), in candidate order (VF pairs,
+ *   then EE pairs): out_kind[i] (CCD_KIND_VF / CCD_KIND_EE), out_pairs[2 i],
+ *   out_pairs[2 i + 1] (the pair's ids) and out_toi[i]; each output holds
+ *   n_vf + n_ee entries.  *n_active (host) receives |C_A|; eps_out (host,
+ *   may be NULL) the 6 eps used.  Synchronizes `stream`.  Returns
+ *   CCD_ERR_CAPACITY when a frontier fell back (answers stay conservative).
+ */
+ccd_status ccd_scene_eps(const double *x0, const double *x1, int64_t nv, double eps[6],
+                         void *workspace, size_t ws_bytes, void *stream);
+size_t ccd_broad_phase_workspace_bytes(int64_t nv, int64_t nf, int64_t ne, int64_t cap_vf,
+                                       int64_t cap_ee);
+ccd_status ccd_broad_phase(const double *x0, const double *x1, int64_t nv, const int32_t *faces,
+                           int64_t nf, const int32_t *edges, int64_t ne, double margin,
+                           int32_t *vf_pairs, int64_t cap_vf, int32_t *ee_pairs, int64_t cap_ee,
+                           int64_t counts[2], void *workspace, size_t ws_bytes, void *stream);
+size_t ccd_active_set_workspace_bytes(int64_t n_cand, int64_t max_itr);
+ccd_status ccd_active_set(const double *x0, const double *x1, int64_t nv, const int32_t *faces,
+                          const int32_t *edges, const int32_t *vf_pairs, int64_t n_vf,
+                          const int32_t *ee_pairs, int64_t n_ee, double delta, int64_t max_itr,
+                          int32_t *out_kind, int32_t *out_pairs, double *out_toi,
+                          int64_t *n_active, double eps_out[6], void *workspace, size_t ws_bytes,
+                          void *stream);
+
+/*
  * Layout helper: copies n queries from an array of structures aos[n][24]
  * (query-major, the same 24-value order) into columns [0, n) of a structure
  * of arrays with plane stride ld >= n: soa[k * ld + i] = aos[i * 24 + k].

@@ -13,12 +13,13 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc", "ccd.cu")
+SRCS = [SRC, os.path.join(HERE, "csrc", "activeset.cu")]
 INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libccd_gb300.so")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
-              "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
+              "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def nvcc() -> str:
@@ -29,7 +30,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return [SRC, os.path.join(INCLUDE, "ccd.h")]
+    return [*SRCS, os.path.join(INCLUDE, "ccd.h")]
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
@@ -38,10 +39,21 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in sources())):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-o", tmp, SRC]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+    objs, procs = [], []
+    for src in SRCS:   # translation units compile in parallel, then one link
+        obj = os.path.join(LIB_DIR, os.path.basename(src) + f".{os.getpid()}.o")
+        cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((subprocess.Popen(cmd), cmd))
+        objs.append(obj)
+    for proc, cmd in procs:
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, cmd)
+    link = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
+    subprocess.run(link, check=True)
+    for obj in objs:
+        os.remove(obj)
     os.replace(tmp, LIB)
     return LIB
 

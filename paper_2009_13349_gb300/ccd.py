@@ -72,6 +72,19 @@ def lib():
         L.ccd_line_search_workspace_bytes.restype = sz
         L.ccd_line_search.argtypes = [dp, i64, i64, ctypes.POINTER(LineSearchIO), vp, sz, vp]
         L.ccd_line_search.restype = ctypes.c_int
+        L.ccd_scene_eps.argtypes = [dp, dp, i64, dp, vp, sz, vp]
+        L.ccd_scene_eps.restype = ctypes.c_int
+        L.ccd_broad_phase_workspace_bytes.argtypes = [i64, i64, i64, i64, i64]
+        L.ccd_broad_phase_workspace_bytes.restype = sz
+        L.ccd_broad_phase.argtypes = [dp, dp, i64, vp, i64, vp, i64, ctypes.c_double, vp, i64,
+                                      vp, i64, ctypes.POINTER(ctypes.c_int64), vp, sz, vp]
+        L.ccd_broad_phase.restype = ctypes.c_int
+        L.ccd_active_set_workspace_bytes.argtypes = [i64, i64]
+        L.ccd_active_set_workspace_bytes.restype = sz
+        L.ccd_active_set.argtypes = [dp, dp, i64, vp, vp, vp, i64, vp, i64, ctypes.c_double,
+                                     i64, vp, vp, dp, ctypes.POINTER(ctypes.c_int64), dp, vp, sz,
+                                     vp]
+        L.ccd_active_set.restype = ctypes.c_int
         L.ccd_aos_to_soa.argtypes = [dp, i64, dp, i64, vp]
         L.ccd_aos_to_soa.restype = ctypes.c_int
         L.ccd_status_str.argtypes = [ctypes.c_int]
@@ -387,6 +400,89 @@ def line_search(verts: torch.Tensor, n_vf: int, n_ee: int, p: float, delta: floa
     return {"alpha": io.alpha, "p": io.p_out, "d": io.d, "d_i": io.d_i, "eps_i": io.eps_i,
             "delta_i": io.delta_i, "passes": io.passes, "validated": bool(io.validated),
             "status": code}
+
+
+def _mesh_args(x0, x1, faces, edges):
+    for t, name, dt in ((x0, "x0", torch.float64), (x1, "x1", torch.float64),
+                        (faces, "faces", torch.int32), (edges, "edges", torch.int32)):
+        _require_cuda(t, name, dt)
+    if x0.shape != x1.shape or x0.dim() != 2 or x0.shape[1] != 3:
+        raise ValueError("x0, x1 are (nv, 3)")
+    if faces.dim() != 2 or faces.shape[1] != 3 or edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("faces are (nf, 3), edges (ne, 2)")
+
+
+def scene_eps(x0: torch.Tensor, x1: torch.Tensor, stream=None) -> np.ndarray:
+    """eps of the scene per kind and axis, (2, 3) on the host (ccd_scene_eps)."""
+    ws = torch.empty(256, dtype=torch.uint8, device=x0.device)
+    eps = (ctypes.c_double * 6)()
+    _check(lib().ccd_scene_eps(_ptr(x0), _ptr(x1), x0.shape[0], eps, _ptr(ws), 256,
+                               _stream(stream)), "ccd_scene_eps")
+    return np.array(list(eps)).reshape(2, 3)
+
+
+def broad_phase(x0, x1, faces, edges, margin: float, cap: int | None = None, stream=None):
+    """Candidate pairs (vf (k, 2), ee (m, 2)) int32 device tensors, sorted
+    (ccd_broad_phase); capacities grow until the lists fit."""
+    _mesh_args(x0, x1, faces, edges)
+    nv, nf, ne = x0.shape[0], faces.shape[0], edges.shape[0]
+    cap_vf = cap_ee = int(cap if cap is not None else 4 * (nv + nf + ne) + 1024)
+    while True:
+        nb = lib().ccd_broad_phase_workspace_bytes(nv, nf, ne, cap_vf, cap_ee)
+        if nb == 0:
+            raise CCDError(-1, "ccd_broad_phase_workspace_bytes")
+        ws = torch.empty(nb, dtype=torch.uint8, device=x0.device)
+        vf = torch.empty((cap_vf, 2), dtype=torch.int32, device=x0.device)
+        ee = torch.empty((cap_ee, 2), dtype=torch.int32, device=x0.device)
+        counts = (ctypes.c_int64 * 2)()
+        code = lib().ccd_broad_phase(_ptr(x0), _ptr(x1), nv, _ptr(faces), nf, _ptr(edges), ne,
+                                     float(margin), _ptr(vf), cap_vf, _ptr(ee), cap_ee, counts,
+                                     _ptr(ws), nb, _stream(stream))
+        if code == -5:
+            cap_vf, cap_ee = max(cap_vf, int(counts[0])), max(cap_ee, int(counts[1]))
+            continue
+        _check(code, "ccd_broad_phase")
+        return vf[:counts[0]], ee[:counts[1]]
+
+
+def active_set(x0, x1, faces, edges, vf, ee, delta: float = 1e-6, max_itr: int = 10**6,
+               stream=None) -> dict:
+    """Algorithm 3 over given candidates (ccd_active_set): kind, pairs, toi
+    of the colliding candidates (device tensors) and the eps used."""
+    _mesh_args(x0, x1, faces, edges)
+    n = vf.shape[0] + ee.shape[0]
+    nb = lib().ccd_active_set_workspace_bytes(n, int(max_itr))
+    if nb == 0:
+        raise CCDError(-1, "ccd_active_set_workspace_bytes")
+    dev = x0.device
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    kind = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    pairs = torch.empty((max(n, 1), 2), dtype=torch.int32, device=dev)
+    toi = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    na = ctypes.c_int64()
+    eps = (ctypes.c_double * 6)()
+    vfc, eec = vf.contiguous(), ee.contiguous()
+    code = lib().ccd_active_set(_ptr(x0), _ptr(x1), x0.shape[0], _ptr(faces), _ptr(edges),
+                                _ptr(vfc), vfc.shape[0], _ptr(eec), eec.shape[0], float(delta),
+                                int(max_itr), _ptr(kind), _ptr(pairs), _ptr(toi),
+                                ctypes.byref(na), eps, _ptr(ws), nb, _stream(stream))
+    if code not in (0, -5):
+        raise CCDError(code, "ccd_active_set")
+    m = na.value
+    return {"kind": kind[:m], "pairs": pairs[:m], "toi": toi[:m],
+            "eps": np.array(list(eps)).reshape(2, 3), "status": code}
+
+
+def construct_active_set(x0, x1, faces, edges, delta: float = 1e-6, max_itr: int = 10**6,
+                         margin: float | None = None, stream=None) -> dict:
+    """Algorithm 3 end to end: scene eps, broad phase with margin (default
+    the largest eps), CCD of every candidate, the colliding ones."""
+    if margin is None:
+        margin = float(scene_eps(x0, x1, stream).max())
+    vf, ee = broad_phase(x0, x1, faces, edges, margin, stream=stream)
+    out = active_set(x0, x1, faces, edges, vf, ee, delta, max_itr, stream)
+    out.update({"vf_candidates": vf, "ee_candidates": ee, "margin": margin})
+    return out
 
 
 def aos_to_soa(aos: torch.Tensor, soa: torch.Tensor, col: int = 0, stream=None) -> None:
