@@ -42,20 +42,23 @@
 #define ORACLE_VF 0
 
 /* Sec. 3, "Multivariate CCD Formulation": linear trajectory
- * p(t) = (1-t) p^0 + t p^1, evaluated as p^0 + (p^1 - p^0) t. */
+ * p(t) = (1-t) p^0 + t p^1, evaluated as p^0 + (p^1 - p^0) t with one
+ * rounding for the product and sum: fma(p^1 - p^0, t, p^0). */
 static double traj(const double *q, int point, int c, double t)
 {
     double x0 = q[point * 3 + c];
     double x1 = q[12 + point * 3 + c];
     double d = x1 - x0;
-    return x0 + d * t;
+    return fma(d, t, x0);
 }
 
-/* Eq. (F-vf) and Eq. (F-ee), written in a fixed operation order:
- *   VF: q = p - v1, e1 = v2 - v1, e2 = v3 - v1;  F = (q - u e1) - v e2
- *       (equals p - ((1-u-v) v1 + u v2 + v v3)).
- *   EE: d1 = p2 - p1, d2 = p4 - p3;  F = (p1 + u d1) - (p3 + v d2)
- *       (equals ((1-u) p1 + u p2) - ((1-v) p3 + v p4)).
+/* Eq. (F-vf) and Eq. (F-ee), written in a fixed operation order (fma is
+ * the correctly rounded fused multiply-add of C99):
+ *   VF: q = p - v1, e1 = v2 - v1, e2 = v3 - v1;
+ *       F = fma(-v, e2, fma(-u, e1, q))   (= p - ((1-u-v) v1 + u v2 + v v3))
+ *   EE: d1 = p2 - p1, d2 = p4 - p3;
+ *       F = fma(u, d1, p1) - fma(v, d2, p3)
+ *                                  (= ((1-u) p1 + u p2) - ((1-v) p3 + v p4))
  * All positions are taken at time t first. */
 void oracle_corner(int kind, const double *q, double t, double u, double v,
                    double F[3])
@@ -69,11 +72,11 @@ void oracle_corner(int kind, const double *q, double t, double u, double v,
             double qq = a - b;   /* p - v1  */
             double e1 = e - b;   /* v2 - v1 */
             double e2 = f - b;   /* v3 - v1 */
-            F[c] = (qq - u * e1) - v * e2;
+            F[c] = fma(-v, e2, fma(-u, e1, qq));
         } else {
             double d1 = b - a;   /* p2 - p1 */
             double d2 = f - e;   /* p4 - p3 */
-            F[c] = (a + u * d1) - (e + v * d2);
+            F[c] = fma(u, d1, a) - fma(v, d2, e);
         }
     }
 }

@@ -50,30 +50,28 @@ def test_err_from_bounds_matches_formula_by_hand():
 
 def _running_bound(kind, ms):
     """Rigorous forward-error bound (gamma = 1) of the oracle's operation
-    order, in units of |value| <= M, with fl(a op b) = (a op b)(1 + theta),
-    |theta| <= u = 2^-53, t, u, v in [0, 1] exact; second-order terms kept."""
+    order, in units of |value| <= M, with fl(a op b) = (a op b)(1 + theta)
+    and fma(s, y, z) = (s y + z)(1 + theta), |theta| <= u = 2^-53, t, u, v in
+    [0, 1] exact; second-order terms kept."""
     u = U
 
-    def add(Ea, Eb, M):   # exact |result| <= M
+    def add(Ea, Eb, M):       # a + b, exact |result| <= M
         return Ea + Eb + u * (M + Ea + Eb)
 
-    def scale(Ea, M):     # multiply by an exact s in [0, 1]
-        return Ea + u * (M + Ea)
+    def fma(Ey, Ez, M):       # s y + z with an exact |s| <= 1, exact |result| <= M
+        return Ey + Ez + u * (M + Ey + Ez)
 
     Ed = add(0, 0, 2)             # x1 - x0
-    Edt = scale(Ed, 2)            # (x1 - x0) t
-    Ex = add(0, Edt, 1)           # x0 + (x1 - x0) t, |x(t)| <= 1
+    Ex = fma(Ed, 0, 1)            # fma(x1 - x0, t, x0), |x(t)| <= 1
     if kind == 0:
         Eq = add(Ex, Ex, 2)       # q = p - v1, e1, e2 alike
-        Eue = scale(Eq, 2)        # u e1 (and v e2)
-        Ea = add(Eq, Eue, 2)      # q - u e1 = p - ((1-u) v1 + u v2)
-        EF = add(Ea, Eue, 4)      # (q - u e1) - v e2, |F| <= 4 off the prism
+        Ea = fma(Eq, Eq, 2)       # fma(-u, e1, q) = p - ((1-u) v1 + u v2)
+        EF = fma(Eq, Ea, 4)       # fma(-v, e2, .), |F| <= 4 off the prism
         M = 4
     else:
         Ed1 = add(Ex, Ex, 2)      # d1 = p2 - p1
-        Eud = scale(Ed1, 2)       # u d1
-        Ea = add(Ex, Eud, 1)      # p1 + u d1 = (1-u) p1 + u p2
-        EF = add(Ea, Ea, 2)
+        Ea = fma(Ed1, Ex, 1)      # fma(u, d1, p1) = (1-u) p1 + u p2
+        EF = add(Ea, Ea, 2)       # a - b
         M = 2
     if ms:
         EF = add(EF, 0, M + 1)    # m - d with d < gamma
@@ -85,11 +83,11 @@ def _running_bound(kind, ms):
 def test_fixed_expression_error_bound_below_filter(kind, ms):
     bound = _running_bound(kind, ms)
     K = Fr(oracle.filter_constant(kind, ms))
-    # per-multiplication underflow (at most 6 products on a path) adds
+    # per-product underflow (at most 6 products on a path) adds
     # < 6 * 2^-1075, far below the slack
     assert bound + 6 * Fr(1, 2**1075) < K
-    # first-order coefficients: 46 u (VF), 42 u (EE) against 60 u / 56 u
-    assert int(bound / U) == (46 if kind == 0 else 42) + (5 if (ms and kind == 0) else 3 if ms else 0)
+    # first-order coefficients: 30 u (VF), 26 u (EE) against 60 u / 56 u
+    assert int(bound / U) == (30 if kind == 0 else 26) + (5 if (ms and kind == 0) else 3 if ms else 0)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
