@@ -27,17 +27,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "CCD queries/sec FP64, 0 false negatives; p50/p99 batch latency; % FP64 peak"
-# FP64 add/sub/mul of the fixed F expression.  A t-quantity evaluation (one t
-# value: 12 positions x0 + dx t = 24 ops, then VF 9 / EE 6 differences) is
-# shared by a run of boxes with equal t_L; a box evaluation from two
-# t-quantity sets costs 2 t x 3 coords x (VF 10 / EE 12) + 3 (w(B)).
-T_OPS = {0: 24 + 9, 1: 24 + 6}
-BOX_OPS = {0: 2 * 3 * 10 + 3, 1: 2 * 3 * 12 + 3}
-# deep solver with shared partials: a u-partial (one t side) is VF q - u e1 /
-# EE p1 + u d1 (3 x 2 ops), a v-partial VF v e2 (3) / EE p3 + v d2 (6); a box
-# then needs only its 8 corner differences (24) and w(B) (3)
-A_OPS = {0: 6, 1: 6}
-B_OPS = {0: 3, 1: 6}
+# FP64 pipe instructions (add, sub, mul or fused multiply-add, one each) of
+# the fixed F expression.  A t-quantity evaluation (one t value: 12 positions
+# fma(dx, t, x0), then VF 9 / EE 6 differences) is shared by a run of boxes
+# with equal t_L; a box evaluated from two t-quantity sets costs, per t and
+# coordinate, VF 2 fma (q - u e1) + 4 fma (- v e2) / EE 2 + 2 fma and 4
+# differences, plus 3 for w(B).
+T_OPS = {0: 12 + 9, 1: 12 + 6}
+BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
+# deep solver with shared partials: a u-partial (one t side) is VF
+# fma(-u, e1, q) / EE fma(u, d1, p1) (3), a v-partial EE fma(v, d2, p3) (3;
+# VF needs none); a box then needs its 8 corners (24: VF fma, EE differences)
+# and w(B) (3)
+A_OPS = {0: 3, 1: 3}
+B_OPS = {0: 0, 1: 3}
 SHARED_BOX_OPS = 24 + 3
 # the same check evaluated on its own (no sharing): 2 t-quantities + box
 OPS_PER_CHECK = {k: 2 * T_OPS[k] + BOX_OPS[k] for k in (0, 1)}
@@ -345,12 +348,12 @@ def run_native(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "roofline": {"bound": "alu", "kernel": names[top], "achieved": achieved / 1e9,
-                     "peak": peak / 1e9, "unit": "GFLOP/s", "frac": achieved / peak,
+                     "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
-                                    "(one FP64 pipe op = one add or mul; -fmad=false)",
-                     "work": "executed FP64 add/sub/mul from the kernel's counters",
-                     "naive_equivalent_gflops": naive / (per_kernel[top] * 1e-3) / 1e9},
+                                    "(one FP64 pipe op = one add, mul or fma)",
+                     "work": "executed FP64 add/sub/mul/fma instructions from the kernel's counters",
+                     "naive_equivalent_gops": naive / (per_kernel[top] * 1e-3) / 1e9},
         "stage_ms_per_step": {names[k]: float(per_kernel[k]) for k in range(4)},
         "counters": {("VF" if b.kind == 0 else "EE"): counters[j] for j, b in enumerate(batches)},
         "checks": {"mean": float(checks.mean()), "p50": float(np.percentile(checks, 50)),

@@ -115,6 +115,7 @@ __device__ __forceinline__ double pow2neg(int k)
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // ---- per-query data ---------------------------------------------------------
 
@@ -182,7 +183,7 @@ __device__ __forceinline__ void t_quantities(const Query &Q, double t, double *o
     // Q lives in shared memory (one copy per block)
     double P[12];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) P[j] = dadd(Q.x0[j], dmul(Q.dx[j], t));
+    for (int j = 0; j < 12; ++j) P[j] = dfma(Q.dx[j], t, Q.x0[j]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (KIND == CCD_KIND_VF) {
@@ -206,7 +207,7 @@ __device__ __forceinline__ void t_quantities_axis(const Query &Q, double t, int 
 {
     double P[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) P[i] = dadd(Q.x0[3 * i + c], dmul(Q.dx[3 * i + c], t));
+    for (int i = 0; i < 4; ++i) P[i] = dfma(Q.dx[3 * i + c], t, Q.x0[3 * i + c]);
     if (KIND == CCD_KIND_VF) {
         out[c] = dsub(P[0], P[1]);
         out[3 + c] = dsub(P[2], P[1]);
@@ -234,13 +235,13 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
             double f0, f1, f2, f3;
             if (KIND == CCD_KIND_VF) {
                 const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
-                const double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
-                const double bl = dmul(vl, e2), br = dmul(vr, e2);
-                f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+                const double al = dfma(-ul, e1, q), ar = dfma(-ur, e1, q);
+                f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
+                f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
             } else {
                 const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
-                const double al = dadd(a, dmul(ul, d1)), ar = dadd(a, dmul(ur, d1));
-                const double bl = dadd(b, dmul(vl, d2)), br = dadd(b, dmul(vr, d2));
+                const double al = dfma(ul, d1, a), ar = dfma(ur, d1, a);
+                const double bl = dfma(vl, d2, b), br = dfma(vr, d2, b);
                 f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
             }
             const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
@@ -263,13 +264,13 @@ __device__ __forceinline__ void corners_keys_side(const double *T, double ul, do
         double f0, f1, f2, f3;
         if (KIND == CCD_KIND_VF) {
             const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
-            const double al = dsub(q, dmul(ul, e1)), ar = dsub(q, dmul(ur, e1));
-            const double bl = dmul(vl, e2), br = dmul(vr, e2);
-            f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+            const double al = dfma(-ul, e1, q), ar = dfma(-ur, e1, q);
+            f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
+            f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
         } else {
             const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
-            const double al = dadd(a, dmul(ul, d1)), ar = dadd(a, dmul(ur, d1));
-            const double bl = dadd(b, dmul(vl, d2)), br = dadd(b, dmul(vr, d2));
+            const double al = dfma(ul, d1, a), ar = dfma(ur, d1, a);
+            const double bl = dfma(vl, d2, b), br = dfma(vr, d2, b);
             f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
         }
         const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
@@ -593,16 +594,17 @@ __device__ __forceinline__ void root_query(const Params &p, long long i, const Q
     load_query(p.verts, p.n, i, Q);
     const double(&eps)[3] = q.eps;
 
-    // Corners of [0,t_max] x [0,1]^2.  At t = 0 the position x0 + dx*0 equals
-    // x0; at t = t_max it is x0 + dx*t_max (x0 + dx when t_max = 1); with u, v
-    // in {0, 1} the products u e1, v e2 are 0 or the factor itself, so these
-    // are the fixed-order values of F.
+    // Corners of [0,t_max] x [0,1]^2.  At t = 0 the position fma(dx, 0, x0)
+    // equals x0 (up to the sign of a zero, which no comparison sees); at
+    // t = t_max it is fma(dx, t_max, x0); with u, v in {0, 1} the fused steps
+    // fma(-u, e1, q) etc. reduce to q or one rounded subtraction, so these are
+    // the fixed-order values of F.
     double F[2][2][2][3];
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
         double P[12];
 #pragma unroll
-        for (int j = 0; j < 12; ++j) P[j] = it ? dadd(Q.x0[j], dmul(Q.dx[j], q.t_max)) : Q.x0[j];
+        for (int j = 0; j < 12; ++j) P[j] = it ? dfma(Q.dx[j], q.t_max, Q.x0[j]) : Q.x0[j];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (KIND == CCD_KIND_VF) {
@@ -709,11 +711,11 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 // ---- shared u/v partials for the deep solver ------------------------------------
 //
 // Within one chunk of a level, boxes of a run share t, and neighbouring boxes
-// share u or v values.  The corner expression splits into a u-partial
-// a(t,u) and a v-partial b(t,v) (VF: a = q - u e1, b = v e2, F = a - b;
-// EE: a = p1 + u d1, b = p3 + v d2, F = a - b), each the same rounded
-// operations the per-box evaluation performs, so computing every distinct
-// partial once per chunk gives bit-identical corners.  Partials are keyed by
+// share u or v values.  The corner expression splits into partials, each the
+// same rounded operations the per-box evaluation performs, so computing every
+// distinct partial once per chunk gives bit-identical corners: VF a u-partial
+// a(t,u) = fma(-u, e1, q) and F = fma(-v, e2(t), a) (no v-partial: e2 is a
+// t-quantity); EE a(t,u) = fma(u, d1, p1), b(t,v) = fma(v, d2, p3), F = a - b.  Partials are keyed by
 // (t value, numerator): the chunk's boxes are in Q order (ascending t_L), so
 // its distinct t values are the runs' left ends plus the right ends that are
 // not the next run's left end, and their dense ids follow from one block
@@ -786,7 +788,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     s.at[tid] = valid ? b.a[0] : ~0ull;
     for (int j = tid; j < SH_SLOTS; j += BS) {
         sh.ukey[j] = SH_EMPTY;
-        sh.vkey[j] = SH_EMPTY;
+        if (KIND == CCD_KIND_EE) sh.vkey[j] = SH_EMPTY;
     }
     __syncthreads();
     // runs of equal t_L, and gaps between consecutive runs' t values
@@ -816,9 +818,11 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
             ku[j] = tk | (b.a[1] + (j & 1));
             su[j] = sh_insert(sh.ukey, ku[j], &fresh);
             if (fresh) ins |= 1u << j;
-            kv[j] = tk | (b.a[2] + (j & 1));
-            sv[j] = sh_insert(sh.vkey, kv[j], &fresh);
-            if (fresh) ins |= 16u << j;
+            if (KIND == CCD_KIND_EE) {   // VF corners need no v-partial
+                kv[j] = tk | (b.a[2] + (j & 1));
+                sv[j] = sh_insert(sh.vkey, kv[j], &fresh);
+                if (fresh) ins |= 16u << j;
+            }
         }
     }
     __syncthreads();
@@ -858,32 +862,40 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
             const double *T = sh.tq[(int)(key >> 54)];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                sh.a[task][c] = KIND == CCD_KIND_VF ? dsub(T[c], dmul(u, T[3 + c]))
-                                                    : dadd(T[c], dmul(u, T[3 + c]));
+                sh.a[task][c] = KIND == CCD_KIND_VF ? dfma(-u, T[3 + c], T[c])
+                                                    : dfma(u, T[3 + c], T[c]);
         } else {
             const int e = task - NU;
             const unsigned long long key = sh.vkey_by_id[e];
             const double v = dyadic(key & SH_VAL_MASK, k[2]);
             const double *T = sh.tq[(int)(key >> 54)];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                sh.b[e][c] = KIND == CCD_KIND_VF ? dmul(v, T[6 + c])
-                                                 : dadd(T[6 + c], dmul(v, T[9 + c]));
+            for (int c = 0; c < 3; ++c) sh.b[e][c] = dfma(v, T[9 + c], T[6 + c]);   // EE only
         }
     }
     __syncthreads();
     if (valid) {
         long long km[3], kM[3];
 #pragma unroll
+        const double vl = dyadic(b.a[2], k[2]), vr = dyadic(b.a[2] + 1, k[2]);
         for (int side = 0; side < 2; ++side) {
             const int u0 = sh.uid[su[2 * side]], u1 = sh.uid[su[2 * side + 1]];
-            const int v0 = sh.vid[sv[2 * side]], v1 = sh.vid[sv[2 * side + 1]];
+            const int v0 = KIND == CCD_KIND_EE ? sh.vid[sv[2 * side]] : 0;
+            const int v1 = KIND == CCD_KIND_EE ? sh.vid[sv[2 * side + 1]] : 0;
+            const double *T = sh.tq[tl + side];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double al = sh.a[u0][c], ar = sh.a[u1][c];
-                const double bl = sh.b[v0][c], br = sh.b[v1][c];
-                const long long k0 = dkey(dsub(al, bl)), k1 = dkey(dsub(al, br));
-                const long long k2 = dkey(dsub(ar, bl)), k3 = dkey(dsub(ar, br));
+                double f0, f1, f2, f3;
+                if (KIND == CCD_KIND_VF) {
+                    const double e2 = T[6 + c];
+                    f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
+                    f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
+                } else {
+                    const double bl = sh.b[v0][c], br = sh.b[v1][c];
+                    f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+                }
+                const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
                 const long long lo = min(min(k0, k1), min(k2, k3));
                 const long long hi = max(max(k0, k1), max(k2, k3));
                 if (side == 0) { km[c] = lo; kM[c] = hi; }
