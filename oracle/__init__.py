@@ -35,7 +35,12 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build (idempotent)."""
+    """Compile the oracle with gcc into oracle/_build (idempotent).  The
+    mutation tests set CCD_ORACLE_LIB to a library built from a deliberately
+    altered copy of ccd_oracle.c; that library is then used instead."""
+    override = os.environ.get("CCD_ORACLE_LIB")
+    if override:
+        return override
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):

@@ -1,0 +1,103 @@
+"""The oracle's pins are not circular: each plausible mistake planted in a
+copy of the oracle's C source makes the pin suite fail.
+
+Every mutant below is a one-spot edit of ``oracle/ccd_oracle.c`` (a dropped
+term, a wrong sign or index, a swapped comparison or constant, a wrong tie
+order ...).  The test builds each mutant into its own library and runs the
+CPU pin files against it (``CCD_ORACLE_LIB``); a mutant that passes them all
+would be a mistake the pins cannot see.  An unmodified copy built the same
+way must pass, which checks the harness itself.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ccd_oracle.c")
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_linesearch.py",
+        "tests/test_oracle_activeset.py"]
+
+MUTANTS = [
+    ("VF corner drops the v e2 term",
+     [("F[c] = fma(-v, e2, fma(-u, e1, qq));", "F[c] = fma(-u, e1, qq);")]),
+    ("EE corner adds instead of subtracting",
+     [("F[c] = fma(u, d1, a) - fma(v, d2, e);", "F[c] = fma(u, d1, a) + fma(v, d2, e);")]),
+    ("VF e2 taken from the wrong vertex",
+     [("double e2 = f - b;   /* v3 - v1 */", "double e2 = e - b;   /* v3 - v1 */")]),
+    ("trajectory reversed in time",
+     [("return fma(d, t, x0);", "return fma(d, 1.0 - t, x0);")]),
+    ("box minimum keeps the maximum",
+     [("if (first || F[c] < m[c]) m[c] = F[c];", "if (first || F[c] > m[c]) m[c] = F[c];")]),
+    ("filter comparisons made strict",
+     [("if (!((m[c] - ms) <= err[c] && (M[c] + ms) >= -err[c])) hit = 0;",
+       "if (!((m[c] - ms) < err[c] && (M[c] + ms) > -err[c])) hit = 0;")]),
+    ("minimum separation moves the box inward",
+     [("if (!((m[c] - ms) <= err[c] && (M[c] + ms) >= -err[c])) hit = 0;",
+       "if (!((m[c] + ms) <= err[c] && (M[c] - ms) >= -err[c])) hit = 0;")]),
+    ("split ties resolved v, then u, then t",
+     [("int dim = (ct == cmax) ? 0 : (cu == cmax) ? 1 : 2;",
+       "int dim = (cv == cmax) ? 2 : (cu == cmax) ? 1 : 0;")]),
+    ("prism cull strict",
+     [("keep1 = I1[2] <= 1.0 - I1[4];", "keep1 = I1[2] < 1.0 - I1[4];"),
+      ("keep2 = I2[2] <= 1.0 - I2[4];", "keep2 = I2[2] < 1.0 - I2[4];")]),
+    ("check limit off by one", [("if (n >= max_itr) {", "if (n > max_itr) {")]),
+    ("VF filter constant replaced by EE's",
+     [("static const double K_VF = 6.661338147750939e-15;",
+       "static const double K_VF = 6.217248937900877e-15;")]),
+    ("time of impact from the right end", [("if (first) If_left = I[0];", "if (first) If_left = I[1];")]),
+    ("only colliding boxes counted",
+     [("        n += 1;\n", ""), ("        if (!hit) continue;\n", "        if (!hit) continue;\n        n += 1;\n")]),
+    ("every terminating box returns", [("int first = (e.level != lp);", "int first = 1;")]),
+    ("queue ordered by descending t",
+     [("if (x->I[0] != y->I[0]) return x->I[0] < y->I[0];",
+       "if (x->I[0] != y->I[0]) return x->I[0] > y->I[0];")]),
+    ("shortened interval not scaled back to t",
+     [("if (result == 1) r_toi = t_max * r_toi;", "if (result == 1) r_toi = r_toi;")]),
+    ("distance skips the hypotenuse edge",
+     [("const int nedge = kind == ORACLE_VF ? 3 : 4;", "const int nedge = kind == ORACLE_VF ? 2 : 4;")]),
+    # (Flipping the sign of the distance's edge zero crossings is not in the
+    # list: those candidates are implied by the pair crossings f_c1 = +-f_c2,
+    # which meet at every point where all three f_c vanish, so that mutant
+    # computes the same distance.)
+    ("distance interior determinant with the wrong sign",
+     [("const double det = a11 * a22 - a12 * a21;", "const double det = a11 * a22 + a12 * a21;")]),
+    ("scene bound without the floor of 1",
+     [("double g[3] = {1.0, 1.0, 1.0};", "double g[3] = {0.0, 0.0, 0.0};")]),
+]
+
+
+def _build(tmp, name, subs):
+    text = open(SRC).read()
+    for old, new in subs:
+        assert text.count(old) == 1, f"{name}: mutation site not unique: {old!r}"
+        text = text.replace(old, new)
+    src = os.path.join(tmp, f"{abs(hash(name))}.c")
+    lib = src[:-2] + ".so"
+    open(src, "w").write(text)
+    subprocess.run(["gcc", *oracle.CFLAGS, "-o", lib, src, "-lm"], check=True)
+    return lib
+
+
+def _run_pins(lib):
+    env = dict(os.environ, CCD_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu", *PINS], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode
+
+
+def test_pins_kill_every_mutant():
+    with tempfile.TemporaryDirectory() as tmp:
+        jobs = [("unmodified", [])] + MUTANTS
+        libs = [_build(tmp, name, subs) for name, subs in jobs]
+        workers = max(1, min(len(jobs), (os.cpu_count() or 2)))
+        with cf.ThreadPoolExecutor(workers) as ex:
+            codes = list(ex.map(_run_pins, libs))
+    assert codes[0] == 0, "the unmodified oracle must pass its pins"
+    survivors = [name for (name, _), c in zip(jobs[1:], codes[1:]) if c == 0]
+    assert not survivors, f"mutants not caught by any pin: {survivors}"
