@@ -49,7 +49,7 @@ constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
 constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
 constexpr int POOL_CAP_MAX = 4096;
-constexpr int POOL_BLOCKS_PER_SM = 8; // ... and one-warp blocks per SM
+constexpr int POOL_BLOCKS_PER_SM = 10; // ... and one-warp blocks per SM (the shared-memory limit)
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM
 constexpr int BIG = 0x7fffffff;
@@ -876,8 +876,8 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     __syncthreads();
     if (valid) {
         long long km[3], kM[3];
-#pragma unroll
         const double vl = dyadic(b.a[2], k[2]), vr = dyadic(b.a[2] + 1, k[2]);
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int u0 = sh.uid[su[2 * side]], u1 = sh.uid[su[2 * side + 1]];
             const int v0 = KIND == CCD_KIND_EE ? sh.vid[sv[2 * side]] : 0;
