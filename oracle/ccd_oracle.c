@@ -57,7 +57,7 @@ static double traj(const double *q, int point, int c, double t)
  *   VF: q = p - v1, e1 = v2 - v1, e2 = v3 - v1;
  *       F = fma(-v, e2, fma(-u, e1, q))   (= p - ((1-u-v) v1 + u v2 + v v3))
  *   EE: d1 = p2 - p1, d2 = p4 - p3;
- *       F = fma(u, d1, p1) - fma(v, d2, p3)
+ *       F = fma(u, d1, p1 - fma(v, d2, p3))
  *                                  (= ((1-u) p1 + u p2) - ((1-v) p3 + v p4))
  * All positions are taken at time t first. */
 void oracle_corner(int kind, const double *q, double t, double u, double v,
@@ -76,7 +76,7 @@ void oracle_corner(int kind, const double *q, double t, double u, double v,
         } else {
             double d1 = b - a;   /* p2 - p1 */
             double d2 = f - e;   /* p4 - p3 */
-            F[c] = fma(u, d1, a) - fma(v, d2, e);
+            F[c] = fma(u, d1, a - fma(v, d2, e));
         }
     }
 }

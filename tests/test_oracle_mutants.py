@@ -26,7 +26,7 @@ MUTANTS = [
     ("VF corner drops the v e2 term",
      [("F[c] = fma(-v, e2, fma(-u, e1, qq));", "F[c] = fma(-u, e1, qq);")]),
     ("EE corner adds instead of subtracting",
-     [("F[c] = fma(u, d1, a) - fma(v, d2, e);", "F[c] = fma(u, d1, a) + fma(v, d2, e);")]),
+     [("F[c] = fma(u, d1, a - fma(v, d2, e));", "F[c] = fma(u, d1, a + fma(v, d2, e));")]),
     ("VF e2 taken from the wrong vertex",
      [("double e2 = f - b;   /* v3 - v1 */", "double e2 = e - b;   /* v3 - v1 */")]),
     ("trajectory reversed in time",

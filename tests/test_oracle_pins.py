@@ -69,9 +69,10 @@ def _running_bound(kind, ms):
         EF = fma(Eq, Ea, 4)       # fma(-v, e2, .), |F| <= 4 off the prism
         M = 4
     else:
-        Ed1 = add(Ex, Ex, 2)      # d1 = p2 - p1
-        Ea = fma(Ed1, Ex, 1)      # fma(u, d1, p1) = (1-u) p1 + u p2
-        EF = add(Ea, Ea, 2)       # a - b
+        Ed1 = add(Ex, Ex, 2)      # d1 = p2 - p1 (and d2)
+        Eb = fma(Ed1, Ex, 1)      # fma(v, d2, p3) = (1-v) p3 + v p4
+        Ec = add(Ex, Eb, 2)       # p1 - b
+        EF = fma(Ed1, Ec, 2)      # fma(u, d1, p1 - b)
         M = 2
     if ms:
         EF = add(EF, 0, M + 1)    # m - d with d < gamma
@@ -86,8 +87,8 @@ def test_fixed_expression_error_bound_below_filter(kind, ms):
     # per-product underflow (at most 6 products on a path) adds
     # < 6 * 2^-1075, far below the slack
     assert bound + 6 * Fr(1, 2**1075) < K
-    # first-order coefficients: 30 u (VF), 26 u (EE) against 60 u / 56 u
-    assert int(bound / U) == (30 if kind == 0 else 26) + (5 if (ms and kind == 0) else 3 if ms else 0)
+    # first-order coefficients: 30 u (VF), 27 u (EE) against 60 u / 56 u
+    assert int(bound / U) == (30 if kind == 0 else 27) + (5 if (ms and kind == 0) else 3 if ms else 0)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
