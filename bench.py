@@ -31,16 +31,15 @@ METRIC = "CCD queries/sec FP64, 0 false negatives; p50/p99 batch latency; % FP64
 # the fixed F expression.  A t-quantity evaluation (one t value: 12 positions
 # fma(dx, t, x0), then VF 9 / EE 6 differences) is shared by a run of boxes
 # with equal t_L; a box evaluated from two t-quantity sets costs, per t and
-# coordinate, VF 2 fma (q - u e1) + 4 fma (- v e2) / EE 2 + 2 fma and 4
-# differences, plus 3 for w(B).
+# coordinate, VF 2 fma (q - u e1) + 4 fma (- v e2) / EE 2 x (fma + difference)
+# (p1 - (p3 + v d2)) + 4 fma (+ u d1), plus 3 for w(B).
 T_OPS = {0: 12 + 9, 1: 12 + 6}
 BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
-# deep solver with shared partials: a u-partial (one t side) is VF
-# fma(-u, e1, q) / EE fma(u, d1, p1) (3), a v-partial EE fma(v, d2, p3) (3;
-# VF needs none); a box then needs its 8 corners (24: VF fma, EE differences)
-# and w(B) (3)
-A_OPS = {0: 3, 1: 3}
-B_OPS = {0: 0, 1: 3}
+# deep solver with shared partials: one partial per (t value, parameter),
+# VF a(t,u) = fma(-u, e1, q) (3), EE c(t,v) = p1 - fma(v, d2, p3) (6); a box
+# then needs only its 8 fused corners (24) and w(B) (3)
+A_OPS = {0: 3, 1: 6}
+B_OPS = {0: 0, 1: 0}
 SHARED_BOX_OPS = 24 + 3
 # the same check evaluated on its own (no sharing): 2 t-quantities + box
 OPS_PER_CHECK = {k: 2 * T_OPS[k] + BOX_OPS[k] for k in (0, 1)}
@@ -54,7 +53,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=20_000)
+    ap.add_argument("--cpu-sample", type=int, default=500_000)
     ap.add_argument("--ref-sample", type=int, default=4_000)
     ap.add_argument("--max-itr", type=int, default=10**6,
                     help="check limit m_I of the simulation-mixed run (profiling cases only)")

@@ -128,16 +128,22 @@ def deep_slot_bytes(max_itr: int) -> int:
     return 2 * (2 * int(max_itr) + 64) * 24
 
 
+# deep-solver slots that ccd_workspace_bytes provides per SM (EE batches run
+# three deep blocks per SM, VF batches two)
+DEEP_SLOTS_PER_SM = 3
+
+
 def workspace(n: int, max_itr: int, device=None, deep_slots: int | None = None) -> torch.Tensor:
     """Caller-owned device workspace for ``n`` queries at check limit
-    ``max_itr``; ``deep_slots`` caps the deep-solver slots (default: two per SM)."""
+    ``max_itr``; ``deep_slots`` caps the deep-solver slots (default: three
+    per SM)."""
     nbytes = workspace_bytes(n, max_itr)
     if nbytes == 0:
         raise CCDError(-1, "ccd_workspace_bytes")
     if deep_slots is not None:
         dev = torch.device(device or "cuda")
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        nbytes -= max(0, 2 * sms - int(deep_slots)) * deep_slot_bytes(max_itr)
+        nbytes -= max(0, DEEP_SLOTS_PER_SM * sms - int(deep_slots)) * deep_slot_bytes(max_itr)
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 

@@ -51,7 +51,9 @@ constexpr int POOL_CAP = 64;          // ... boxes per level per query (default)
 constexpr int POOL_CAP_MAX = 4096;
 constexpr int POOL_BLOCKS_PER_SM = 10; // ... and one-warp blocks per SM (the shared-memory limit)
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
-constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM
+constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM: VF and
+constexpr int DEEP_BLOCKS_PER_SM_EE = 3;  // EE (80 registers without spills); the segmented
+                                        // kernel, which runs both kinds, keeps 2
 constexpr int BIG = 0x7fffffff;
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
@@ -240,9 +242,9 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
                 f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
             } else {
                 const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
-                const double al = dfma(ul, d1, a), ar = dfma(ur, d1, a);
-                const double bl = dfma(vl, d2, b), br = dfma(vr, d2, b);
-                f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+                const double cl = dsub(a, dfma(vl, d2, b)), cr = dsub(a, dfma(vr, d2, b));
+                f0 = dfma(ul, d1, cl); f1 = dfma(ul, d1, cr);
+                f2 = dfma(ur, d1, cl); f3 = dfma(ur, d1, cr);
             }
             const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
             const long long lo = min(min(k0, k1), min(k2, k3));
@@ -269,9 +271,9 @@ __device__ __forceinline__ void corners_keys_side(const double *T, double ul, do
             f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
         } else {
             const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
-            const double al = dfma(ul, d1, a), ar = dfma(ur, d1, a);
-            const double bl = dfma(vl, d2, b), br = dfma(vr, d2, b);
-            f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
+            const double cl = dsub(a, dfma(vl, d2, b)), cr = dsub(a, dfma(vr, d2, b));
+            f0 = dfma(ul, d1, cl); f1 = dfma(ul, d1, cr);
+            f2 = dfma(ur, d1, cl); f3 = dfma(ur, d1, cr);
         }
         const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
         const long long lo = min(min(k0, k1), min(k2, k3));
@@ -619,11 +621,12 @@ __device__ __forceinline__ void root_query(const Params &p, long long i, const Q
             } else {
                 double d1 = dsub(P[3 + c], P[c]);
                 double d2 = dsub(P[9 + c], P[6 + c]);
-                double a1 = dadd(P[c], d1), b1 = dadd(P[6 + c], d2);
-                F[it][0][0][c] = dsub(P[c], P[6 + c]);
-                F[it][1][0][c] = dsub(a1, P[6 + c]);
-                F[it][0][1][c] = dsub(P[c], b1);
-                F[it][1][1][c] = dsub(a1, b1);
+                double c0 = dsub(P[c], P[6 + c]);                 // v = 0: p1 - p3
+                double c1 = dsub(P[c], dadd(d2, P[6 + c]));       // v = 1: p1 - (p3 + d2)
+                F[it][0][0][c] = c0;
+                F[it][0][1][c] = c1;
+                F[it][1][0][c] = dadd(d1, c0);
+                F[it][1][1][c] = dadd(d1, c1);
             }
         }
     }
@@ -708,35 +711,36 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
     }
 }
 
-// ---- shared u/v partials for the deep solver ------------------------------------
+// ---- shared partials for the deep solver ----------------------------------------
 //
 // Within one chunk of a level, boxes of a run share t, and neighbouring boxes
-// share u or v values.  The corner expression splits into partials, each the
-// same rounded operations the per-box evaluation performs, so computing every
-// distinct partial once per chunk gives bit-identical corners: VF a u-partial
-// a(t,u) = fma(-u, e1, q) and F = fma(-v, e2(t), a) (no v-partial: e2 is a
-// t-quantity); EE a(t,u) = fma(u, d1, p1), b(t,v) = fma(v, d2, p3), F = a - b.  Partials are keyed by
-// (t value, numerator): the chunk's boxes are in Q order (ascending t_L), so
-// its distinct t values are the runs' left ends plus the right ends that are
-// not the next run's left end, and their dense ids follow from one block
-// scan (t_L of run r has id r + gaps up to r; t_R has that id + 1).  Distinct
-// keys are found with shared-memory hash tables; dense partial ids come from
-// a second block scan; tasks are packed into consecutive lanes.  A chunk
-// with more than SH_RUN_CAP runs or SH_ENTRY_CAP distinct u or v partials is
-// evaluated per box instead.
+// share u or v values.  The corner expression splits into a partial of one
+// parameter at one t and a fused step with the other, each the same rounded
+// operations the per-box evaluation performs, so computing every distinct
+// partial once per chunk gives bit-identical corners:
+//   VF  partial a(t,u) = fma(-u, e1, q),        corner F = fma(-v, e2(t), a);
+//   EE  partial c(t,v) = p1 - fma(v, d2, p3),   corner F = fma(u, d1(t), c);
+// e2 and d1 are t-quantities, so each kind needs one partial table, keyed by
+// (t value, numerator of u for VF / of v for EE).  The chunk's boxes are in
+// Q order (ascending t_L), so its distinct t values are the runs' left ends
+// plus the right ends that are not the next run's left end, and their dense
+// ids follow from one block scan (t_L of run r has id r + gaps up to r; t_R
+// has that id + 1).  Distinct keys are found with a shared-memory hash
+// table; dense partial ids come from a second block scan; tasks are packed
+// into consecutive lanes.  A chunk with more than SH_RUN_CAP runs or
+// SH_ENTRY_CAP distinct partials is evaluated per box instead.
 constexpr int SH_RUN_CAP = 96;
 constexpr int SH_TV_CAP = 2 * SH_RUN_CAP;           // distinct t values per chunk
-constexpr int SH_ENTRY_CAP = 640;                   // partials per table (one t value each)
-constexpr int SH_SLOTS = 2048;                      // per table, power of two
+constexpr int SH_ENTRY_CAP = 640;                   // partials (one t value each)
+constexpr int SH_SLOTS = 2048;                      // hash slots, power of two
 constexpr unsigned long long SH_EMPTY = ~0ull;
 constexpr unsigned long long SH_VAL_MASK = (1ull << 54) - 1;
 
 struct SharedUV {
-    unsigned long long ukey[SH_SLOTS], vkey[SH_SLOTS];
-    int uid[SH_SLOTS], vid[SH_SLOTS];
-    unsigned long long ukey_by_id[SH_ENTRY_CAP], vkey_by_id[SH_ENTRY_CAP];
-    double a[SH_ENTRY_CAP][3];
-    double b[SH_ENTRY_CAP][3];
+    unsigned long long key[SH_SLOTS];
+    int id[SH_SLOTS];
+    unsigned long long key_by_id[SH_ENTRY_CAP];
+    double part[SH_ENTRY_CAP][3];
     double tq[SH_TV_CAP][12];
 };
 
@@ -772,24 +776,22 @@ __device__ __forceinline__ void eval_box_private(const Query &Q, const QP &q,
     box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
 }
 
-// One chunk (one box per thread) through shared u/v partials.
+// One chunk (one box per thread) through shared partials.
 template <int KIND, int BS>
 __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
                                                   const Thresholds &TH, const int (&k)[3],
                                                   bool valid, const Box &b, long long nvalid,
                                                   Smem<BS> &s, SharedUV &sh, BoxTest &bt,
                                                   unsigned long long &tqs,
-                                                  unsigned long long &atasks,
-                                                  unsigned long long &btasks,
+                                                  unsigned long long &ptasks,
                                                   unsigned long long &shared_evals)
 {
     static_assert(4 * BS <= SH_SLOTS, "every insert finds its key or an empty slot");
+    constexpr int PD = KIND == CCD_KIND_VF ? 1 : 2;   // the partial's parameter: u or v
+    constexpr int FD = 3 - PD;                        // the fused one: v or u
     const int tid = threadIdx.x;
     s.at[tid] = valid ? b.a[0] : ~0ull;
-    for (int j = tid; j < SH_SLOTS; j += BS) {
-        sh.ukey[j] = SH_EMPTY;
-        if (KIND == CCD_KIND_EE) sh.vkey[j] = SH_EMPTY;
-    }
+    for (int j = tid; j < SH_SLOTS; j += BS) sh.key[j] = SH_EMPTY;
     __syncthreads();
     // runs of equal t_L, and gaps between consecutive runs' t values
     const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
@@ -807,36 +809,27 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     const int tl = (pk & 0xffff) + (start ? 0 : -1) + (pk >> 16) + (gap ? 1 : 0);   // id of t_L
     if (start) s.run_at[tl] = b.a[0];
     if (open_r) s.run_at[tl + 1] = b.a[0] + 1;     // t_R not shared with the next run
-    int su[4] = {0, 0, 0, 0}, sv[4] = {0, 0, 0, 0};
+    int sk[4] = {0, 0, 0, 0};
     unsigned ins = 0;
-    unsigned long long ku[4] = {0, 0, 0, 0}, kv[4] = {0, 0, 0, 0};
+    unsigned long long kk[4] = {0, 0, 0, 0};
     if (valid) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {   // j = 2 * side + d
-            const unsigned long long tk = (unsigned long long)(tl + (j >> 1)) << 54;
             bool fresh;
-            ku[j] = tk | (b.a[1] + (j & 1));
-            su[j] = sh_insert(sh.ukey, ku[j], &fresh);
+            kk[j] = ((unsigned long long)(tl + (j >> 1)) << 54) | (b.a[PD] + (j & 1));
+            sk[j] = sh_insert(sh.key, kk[j], &fresh);
             if (fresh) ins |= 1u << j;
-            if (KIND == CCD_KIND_EE) {   // VF corners need no v-partial
-                kv[j] = tk | (b.a[2] + (j & 1));
-                sv[j] = sh_insert(sh.vkey, kv[j], &fresh);
-                if (fresh) ins |= 16u << j;
-            }
         }
     }
     __syncthreads();
-    const int pack =
-        block_scan_1sync<BS>(__popc(ins & 15u) | (__popc(ins >> 4) << 16), &tot, s.scan_b);
-    const int NU = tot & 0xffff, NV = tot >> 16;
-    const bool share = NU <= SH_ENTRY_CAP && NV <= SH_ENTRY_CAP;   // block-uniform
+    const int pack = block_scan_1sync<BS>(__popc(ins), &tot, s.scan_b);
+    const int NP = tot;
+    const bool share = NP <= SH_ENTRY_CAP;   // block-uniform
     if (share) {
-        int iu = pack & 0xffff, iv = pack >> 16;
+        int ip = pack;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (ins & (1u << j)) { sh.uid[su[j]] = iu; sh.ukey_by_id[iu] = ku[j]; ++iu; }
-            if (ins & (16u << j)) { sh.vid[sv[j]] = iv; sh.vkey_by_id[iv] = kv[j]; ++iv; }
-        }
+        for (int j = 0; j < 4; ++j)
+            if (ins & (1u << j)) { sh.id[sk[j]] = ip; sh.key_by_id[ip] = kk[j]; ++ip; }
         // one task per (t value, axis): the FP64 work of this phase spreads
         // over 3x the warps (and so over all four SM sub-partitions)
         tqs += (unsigned long long)ntv;
@@ -852,49 +845,33 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
         return;
     }
-    atasks += (unsigned long long)NU;
-    btasks += (unsigned long long)NV;
+    ptasks += (unsigned long long)NP;
     shared_evals += (unsigned long long)nvalid;
-    for (int task = tid; task < NU + NV; task += BS) {
-        if (task < NU) {
-            const unsigned long long key = sh.ukey_by_id[task];
-            const double u = dyadic(key & SH_VAL_MASK, k[1]);
-            const double *T = sh.tq[(int)(key >> 54)];
+    for (int task = tid; task < NP; task += BS) {
+        const unsigned long long key = sh.key_by_id[task];
+        const double x = dyadic(key & SH_VAL_MASK, k[PD]);
+        const double *T = sh.tq[(int)(key >> 54)];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                sh.a[task][c] = KIND == CCD_KIND_VF ? dfma(-u, T[3 + c], T[c])
-                                                    : dfma(u, T[3 + c], T[c]);
-        } else {
-            const int e = task - NU;
-            const unsigned long long key = sh.vkey_by_id[e];
-            const double v = dyadic(key & SH_VAL_MASK, k[2]);
-            const double *T = sh.tq[(int)(key >> 54)];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh.b[e][c] = dfma(v, T[9 + c], T[6 + c]);   // EE only
-        }
+        for (int c = 0; c < 3; ++c)
+            sh.part[task][c] = KIND == CCD_KIND_VF ? dfma(-x, T[3 + c], T[c])
+                                                   : dsub(T[c], dfma(x, T[9 + c], T[6 + c]));
     }
     __syncthreads();
     if (valid) {
         long long km[3], kM[3];
-        const double vl = dyadic(b.a[2], k[2]), vr = dyadic(b.a[2] + 1, k[2]);
+        const double yl = dyadic(b.a[FD], k[FD]), yr = dyadic(b.a[FD] + 1, k[FD]);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const int u0 = sh.uid[su[2 * side]], u1 = sh.uid[su[2 * side + 1]];
-            const int v0 = KIND == CCD_KIND_EE ? sh.vid[sv[2 * side]] : 0;
-            const int v1 = KIND == CCD_KIND_EE ? sh.vid[sv[2 * side + 1]] : 0;
+            const int i0 = sh.id[sk[2 * side]], i1 = sh.id[sk[2 * side + 1]];
             const double *T = sh.tq[tl + side];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double al = sh.a[u0][c], ar = sh.a[u1][c];
-                double f0, f1, f2, f3;
-                if (KIND == CCD_KIND_VF) {
-                    const double e2 = T[6 + c];
-                    f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
-                    f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
-                } else {
-                    const double bl = sh.b[v0][c], br = sh.b[v1][c];
-                    f0 = dsub(al, bl); f1 = dsub(al, br); f2 = dsub(ar, bl); f3 = dsub(ar, br);
-                }
+                const double p0 = sh.part[i0][c], p1 = sh.part[i1][c];
+                // VF: fma(-v, e2, a); EE: fma(u, d1, c)
+                const double g = KIND == CCD_KIND_VF ? T[6 + c] : T[3 + c];
+                const double ml = KIND == CCD_KIND_VF ? -yl : yl, mr = KIND == CCD_KIND_VF ? -yr : yr;
+                const double f0 = dfma(ml, g, p0), f1 = dfma(mr, g, p0);
+                const double f2 = dfma(ml, g, p1), f3 = dfma(mr, g, p1);
                 const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
                 const long long lo = min(min(k0, k1), min(k2, k3));
                 const long long hi = max(max(k0, k1), max(k2, k3));
@@ -957,8 +934,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (valid) b = cur[i];
             if (BS > 32) {
                 eval_chunk_shared<KIND, BS>(Q, q, TH, k, valid, b, min((long long)BS, size - base),
-                                            s, *(SharedUV *)tq, bt, tqs, atasks, btasks,
-                                            shared_evals);
+                                            s, *(SharedUV *)tq, bt, tqs, atasks, shared_evals);
             } else {
             // Boxes are in Q order, so equal t_L form contiguous runs: the
             // t-quantities at t_L and t_R are computed once per run.
@@ -1151,7 +1127,9 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 // level it reached in out_level when that is not null (one-warp tier only;
 // the deep tier answers it through the capacity fallback).
 template <int KIND, int BS>
-__global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
+__global__ void __launch_bounds__(BS, BS == 256 ? (KIND == CCD_KIND_EE ? DEEP_BLOCKS_PER_SM_EE
+                                                                    : DEEP_BLOCKS_PER_SM)
+                                              : 1)
     solve_kernel(Params p, int deep, Box *slots, long long cap, const int *list,
                  const int *count, int *head, int *out_list, unsigned char *out_level,
                  int *out_count)
@@ -1987,7 +1965,8 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
     const size_t per = sizeof(Box) * 2 * (size_t)want;
     long long nb = (long long)(room / per);
     if (nb >= 1) {
-        L.nb_deep = (int)(nb < (long long)DEEP_BLOCKS_PER_SM * sms ? nb : (long long)DEEP_BLOCKS_PER_SM * sms);
+        const long long most = (long long)DEEP_BLOCKS_PER_SM_EE * sms;
+        L.nb_deep = (int)(nb < most ? nb : most);
         L.cap_deep = want;
     } else {
         L.nb_deep = 1;
@@ -2051,8 +2030,14 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
     if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return CCD_ERR_CUDA;
+    {   // resident deep blocks per SM for this kind
+        const int per_sm = KIND == CCD_KIND_EE ? DEEP_BLOCKS_PER_SM_EE : DEEP_BLOCKS_PER_SM;
+        if (L.nb_deep > per_sm * sms) L.nb_deep = per_sm * sms;
+    }
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
         p.over_level, &h->overflow);
@@ -2077,7 +2062,7 @@ size_t ccd_workspace_bytes(int64_t n, int64_t max_itr)
     if (sms <= 0) return 0;
     Layout L = layout_fixed(n, sms);
     return L.off_deep +
-           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM * sms);
+           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM_EE * sms);
 }
 
 ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err, int err_stride,

@@ -173,7 +173,7 @@ def test_capacity_fallback_is_conservative(ccd):
     n, max_itr = b.n, 10**6
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     full = ccd.workspace_bytes(n, max_itr)
-    deep = 2 * sms * ccd.deep_slot_bytes(max_itr)
+    deep = ccd.DEEP_SLOTS_PER_SM * sms * ccd.deep_slot_bytes(max_itr)
     ws = torch.empty(full - deep + 2 * 1024 * 24, dtype=torch.uint8, device="cuda")
     g, e = gpu_run(ccd, b.kind, b.verts, ws=ws)
     st, fb = ccd.workspace_status(ws)
