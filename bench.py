@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=500_000)
-    ap.add_argument("--ref-sample", type=int, default=4_000)
+    ap.add_argument("--ref-sample", type=int, default=50_000)
     ap.add_argument("--max-itr", type=int, default=10**6,
                     help="check limit m_I of the simulation-mixed run (profiling cases only)")
     ap.add_argument("--no-e2e", action="store_true")
