@@ -27,6 +27,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "CCD queries/sec FP64, 0 false negatives; p50/p99 batch latency; % FP64 peak"
+# The paper's own average times per query (its "Ours" rows, Sec. 5 results
+# table) on the CPU it names: context only, a different dataset and machine.
+PAPER_CONTEXT = {
+    "cpu": "AMD EPYC 7452 at 2.35 GHz, C++ with AVX2, per-query averages (one core implied)",
+    "simulation_us_per_query": {"VF": 0.74, "EE": 0.78},
+    "handcrafted_us_per_query": {"VF": 1532.54, "EE": 3029.83},
+    "note": "the paper's datasets are not available here; the synthetic workloads differ",
+}
 # FP64 pipe instructions (add, sub, mul or fused multiply-add, one each) of
 # the fixed F expression.  A t-quantity evaluation (one t value: 12 positions
 # fma(dx, t, x0), then VF 9 / EE 6 differences) is shared by a run of boxes
@@ -360,6 +368,7 @@ def run_native(args):
                    "early_termination_pct": float(100.0 * np.mean(checks >= args.max_itr))},
         "false_negatives": fn, "toi_after_truth": toi_bad,
         "gpu_launches": args.steps * len(batches) * 8,
+        "paper_context": PAPER_CONTEXT,
         "clocks": clk,
     }
 
