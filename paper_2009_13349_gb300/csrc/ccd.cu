@@ -49,7 +49,8 @@ constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
 constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
 constexpr int POOL_CAP_MAX = 4096;
-constexpr int POOL_BLOCKS_PER_SM = 10; // ... and one-warp blocks per SM (the shared-memory limit)
+constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
+                                       // launch takes what the occupancy calculator allows)
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM: VF and
 constexpr int DEEP_BLOCKS_PER_SM_EE = 3;  // EE (80 registers without spills); the segmented
@@ -87,7 +88,7 @@ struct Header {
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
 struct Layout {
-    size_t off_surv, off_mid, off_over, off_level, off_dlist, off_kappa, off_pool, off_small,
+    size_t off_surv, off_mid, off_over, off_level, off_dlist, off_kappa, off_pool, off_meta, off_small,
         off_deep, total;
     int nb_pool, nb_small, nb_deep;
     long long cap_small, cap_deep;
@@ -1241,17 +1242,23 @@ struct PoolSlot {
     int k[3], sd, can_split, found, nn, np, buf;
 };
 
+// A slot's query record lives in global memory (one per slot of the
+// workspace) and is read through L1; keeping it out of shared memory lets
+// about twice as many pooled warps reside on an SM.
+struct PoolMeta {
+    Query Q;
+    QP qp;
+    double kap[3];
+};
+
+template <int KIND>
 struct PoolShared {
     PoolSlot st[POOL_SLOTS];
-    Query Q[POOL_SLOTS];
-    QP qp[POOL_SLOTS];
-    Thresholds TH[POOL_SLOTS];
-    double kap[POOL_SLOTS][3];
     Box box[32];
     double w[32];
     int hit[32], term[32], lane_slot[32], lane_off[32];
     // distinct t values of an iteration (at most 32 runs + 31 gaps + 1)
-    double tq[64][12];
+    double tq[64][TWidth<KIND>::W];
     unsigned long long tv_a[64];
     int tv_slot[64];
 };
@@ -1273,13 +1280,14 @@ __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[
 // segment and queries of the other kind are skipped (one launch per kind).
 template <int KIND>
 __global__ void __launch_bounds__(32)
-    pool_kernel(Params p, Box *mem, int cap, const int *list, const int *count_p, int *head,
-                const ccd_segment *segs, int nseg)
+    pool_kernel(Params p, Box *mem, PoolMeta *metas, int cap, const int *list, const int *count_p,
+                int *head, const ccd_segment *segs, int nseg)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ PoolShared sh;
+    __shared__ PoolShared<KIND> sh;
     const int lane = threadIdx.x;
     PoolSlot &S = sh.st[lane];                     // the slot this lane owns
+    PoolMeta *const meta = metas + (size_t)blockIdx.x * POOL_SLOTS;   // the warp's slots
     Box *const mine = mem + ((size_t)blockIdx.x * POOL_SLOTS + lane) * 3 * (size_t)cap;
     const int count = *(volatile const int *)count_p;
     bool drained = false;
@@ -1306,16 +1314,15 @@ __global__ void __launch_bounds__(32)
                     if (segs) {
                         const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
                         mine_kind = sg.kind == KIND;
-                        if (mine_kind) sh.qp[lane] = qp_segment(sg);
+                        if (mine_kind) meta[lane].qp = qp_segment(sg);
                     } else {
-                        sh.qp[lane] = qp_single(p, qi);
+                        meta[lane].qp = qp_single(p, qi);
                     }
                 }
                 if (idx < count && mine_kind) {
-                    load_query(p.verts, p.n, qi, sh.Q[lane]);
-                    make_thresholds(sh.qp[lane].eps, sh.qp[lane].delta, sh.TH[lane]);
+                    load_query(p.verts, p.n, qi, meta[lane].Q);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) sh.kap[lane][c] = p.kappa[3 * qi + c];
+                    for (int c = 0; c < 3; ++c) meta[lane].kap[c] = p.kappa[3 * qi + c];
                     S.qi = qi;
                     S.size = 1;
                     S.pos = 0;
@@ -1324,7 +1331,7 @@ __global__ void __launch_bounds__(32)
                     S.nn = S.np = 0;
                     S.buf = 0;
                     S.k[0] = S.k[1] = S.k[2] = 0;
-                    pool_split_dim(S, sh.kap[lane]);
+                    pool_split_dim(S, meta[lane].kap);
                     mine[0] = Box{{0ull, 0ull, 0ull}};
                 } else if (idx >= count) {
                     drained = true;
@@ -1396,7 +1403,7 @@ __global__ void __launch_bounds__(32)
         for (int task = lane; task < 3 * ntv; task += 32) {
             const int tv = task / 3;
             const int s2 = sh.tv_slot[tv];
-            t_quantities_axis<KIND>(sh.Q[s2], dmul(sh.qp[s2].t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
+            t_quantities_axis<KIND>(meta[s2].Q, dmul(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
                                     task - 3 * tv, sh.tq[tv]);
         }
         __syncwarp();
@@ -1406,7 +1413,9 @@ __global__ void __launch_bounds__(32)
             corners_keys<KIND>(sh.tq[tl], sh.tq[tl + 1], dyadic(b.a[1], T.k[1]),
                                dyadic(b.a[1] + 1, T.k[1]), dyadic(b.a[2], T.k[2]),
                                dyadic(b.a[2] + 1, T.k[2]), km, kM);
-            box_test_keys(km, kM, sh.TH[so], sh.qp[so].ms, bt.hit, bt.term, bt.w);
+            Thresholds TH;   // a few integer operations: cheaper than keeping 32 in shared memory
+            make_thresholds(meta[so].qp.eps, meta[so].qp.delta, TH);
+            box_test_keys(km, kM, TH, meta[so].qp.ms, bt.hit, bt.term, bt.w);
         }
         sh.box[lane] = b;
         sh.hit[lane] = bt.hit;
@@ -1416,7 +1425,7 @@ __global__ void __launch_bounds__(32)
 
         // 4. the owner lane applies Algorithm 2 to its boxes, in Q order
         if (take > 0) {
-            const QP &qq = sh.qp[lane];
+            const QP &qq = meta[lane].qp;
             Box *cur = mine + (S.buf ? cap : 0);
             Box *nxt = mine + (S.buf ? 0 : cap);
             Box *pend = mine + 2 * (size_t)cap;
@@ -1495,7 +1504,7 @@ __global__ void __launch_bounds__(32)
                         S.k[S.sd] += 1;
                         S.pos = 0;
                         S.found = 0;
-                        pool_split_dim(S, sh.kap[lane]);
+                        pool_split_dim(S, meta[lane].kap);
                     }
                 }
             }
@@ -1504,6 +1513,19 @@ __global__ void __launch_bounds__(32)
     }
     atomicAdd(&p.hdr->evals_pool, evals);
     atomicAdd(&p.hdr->checks_pool, checks_done);
+}
+
+// Resident pooled blocks per SM (its shared memory and registers decide),
+// at most POOL_BLOCKS_PER_SM, times the SM count.
+template <typename K>
+int pool_blocks(K kernel, int sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (per_sm > POOL_BLOCKS_PER_SM) per_sm = POOL_BLOCKS_PER_SM;
+    return per_sm * sms;
 }
 
 // ---- multi-instance (segmented) kernels ---------------------------------------
@@ -1948,6 +1970,8 @@ Layout layout_fixed(long long n, int sms)
     L.nb_pool = sms * POOL_BLOCKS_PER_SM;
     L.off_pool = off;
     off = align256(off + sizeof(Box) * 3 * (size_t)POOL_CAP * POOL_SLOTS * (size_t)L.nb_pool);
+    L.off_meta = off;
+    off = align256(off + sizeof(PoolMeta) * POOL_SLOTS * (size_t)L.nb_pool);
     L.nb_small = sms * SMALL_BLOCKS_PER_SM;
     L.cap_small = SMALL_CAP;
     L.off_small = off; off = align256(off + sizeof(Box) * 2 * (size_t)SMALL_CAP * L.nb_small);
@@ -2023,8 +2047,10 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     stage_mark(0, st);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
-    pool_kernel<KIND><<<L.nb_pool, 32, 0, st>>>(p, (Box *)(ws + L.off_pool), POOL_CAP, p.surv,
-                                                &h->survivors, &h->head_pool, nullptr, 0);
+    const int nb_pool = pool_blocks(pool_kernel<KIND>, sms);
+    pool_kernel<KIND><<<nb_pool, 32, 0, st>>>(p, (Box *)(ws + L.off_pool),
+                                              (PoolMeta *)(ws + L.off_meta), POOL_CAP, p.surv,
+                                              &h->survivors, &h->head_pool, nullptr, 0);
     stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
     const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
@@ -2240,13 +2266,16 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
     off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
     off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
                              (size_t)(sms * POOL_BLOCKS_PER_SM));   // pooled-solver slots
+    off = align256(off + sizeof(PoolMeta) * POOL_SLOTS *
+                             (size_t)(sms * POOL_BLOCKS_PER_SM));   // their query records
     off = align256(off + sizeof(Box) * 2 * (size_t)T.small_cap * (size_t)(sms * T.small_blocks_per_sm));
     return off;
 }
 
 template <int DT>
 ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int nseg, char *ws,
-                                Box *pool_mem, int nb_pool, int pool_cap, size_t off_small,
+                                Box *pool_mem, PoolMeta *pool_meta, int sms, int pool_cap,
+                                size_t off_small,
                                 int nb_small,
                                 long long cap_small, size_t off_deep, int nb_deep,
                                 long long cap_deep, cudaStream_t st)
@@ -2257,12 +2286,11 @@ ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int ns
                              (int)tq_deep) != cudaSuccess)
         return CCD_ERR_CUDA;
     // pooled stage: one launch per kind over the survivor list
-    pool_kernel<CCD_KIND_VF><<<nb_pool, 32, 0, st>>>(p, pool_mem, pool_cap, p.surv,
-                                                     &p.hdr->survivors, &p.hdr->head_pool, segs,
-                                                     nseg);
-    pool_kernel<CCD_KIND_EE><<<nb_pool, 32, 0, st>>>(p, pool_mem, pool_cap, p.surv,
-                                                     &p.hdr->survivors, &p.hdr->head_pool_ee,
-                                                     segs, nseg);
+    pool_kernel<CCD_KIND_VF><<<pool_blocks(pool_kernel<CCD_KIND_VF>, sms), 32, 0, st>>>(
+        p, pool_mem, pool_meta, pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool, segs, nseg);
+    pool_kernel<CCD_KIND_EE><<<pool_blocks(pool_kernel<CCD_KIND_EE>, sms), 32, 0, st>>>(
+        p, pool_mem, pool_meta, pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool_ee, segs,
+        nseg);
     stage_mark(2, st);
     solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
         p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
@@ -2312,6 +2340,8 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     Box *pool_mem = (Box *)(ws + off);
     off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
                              (size_t)(sms * POOL_BLOCKS_PER_SM));
+    PoolMeta *pool_meta = (PoolMeta *)(ws + off);
+    off = align256(off + sizeof(PoolMeta) * POOL_SLOTS * (size_t)(sms * POOL_BLOCKS_PER_SM));
     const size_t off_small = off;
     const int nb_small = sms * T.small_blocks_per_sm;
 
@@ -2321,13 +2351,13 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
         p, segs, nseg);
     stage_mark(1, st);
     ccd_status r = T.deep_threads == 256
-                       ? launch_multi_solvers<256>(p, segs, nseg, ws, pool_mem,
-                                                   sms * POOL_BLOCKS_PER_SM, T.pool_cap,
+                       ? launch_multi_solvers<256>(p, segs, nseg, ws, pool_mem, pool_meta,
+                                                   sms, T.pool_cap,
                                                    off_small, nb_small,
                                                    T.small_cap, fixed, (int)nb_deep,
                                                    deep_cap(max_itr_bound), st)
-                       : launch_multi_solvers<512>(p, segs, nseg, ws, pool_mem,
-                                                   sms * POOL_BLOCKS_PER_SM, T.pool_cap,
+                       : launch_multi_solvers<512>(p, segs, nseg, ws, pool_mem, pool_meta,
+                                                   sms, T.pool_cap,
                                                    off_small, nb_small,
                                                    T.small_cap, fixed, (int)nb_deep,
                                                    deep_cap(max_itr_bound), st);
