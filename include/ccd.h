@@ -139,8 +139,9 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * of queries it handed on), [6] the same for the deep solver, [7] status,
  * [8] t-quantity evaluations (positions and edge vectors at one t, shared by
  * a run of boxes with equal t_L) by the small-frontier solver, [9] the same
- * for the deep solver, [10] shared u-partials and [11] shared v-partials
- * computed by the deep solver (one t side each), [12] deep box evaluations
+ * for the deep solver, [10] shared partials computed by the deep solver (one
+ * per t value and parameter value: u for VF, v for EE), [11] always 0 (kept
+ * for the layout), [12] deep box evaluations
  * that used the shared partials, [13] queries the pooled solver handed to
  * the one-warp solver, [14] sum of check counts n of queries finished by
  * the pooled solver, [15] box evaluations executed by the pooled solver
