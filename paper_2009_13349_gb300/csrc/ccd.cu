@@ -55,7 +55,6 @@ constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM: VF and
 constexpr int DEEP_BLOCKS_PER_SM_EE = 3;  // EE (80 registers without spills); the segmented
                                         // kernel, which runs both kinds, keeps 2
-constexpr int BIG = 0x7fffffff;
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
 struct Box {
@@ -77,8 +76,8 @@ struct Header {
     unsigned long long evals_deep;    // box evaluations executed by the deep solver
     unsigned long long tq_small;      // t-quantity evaluations by the small solver
     unsigned long long tq_deep;       // t-quantity evaluations by the deep solver
-    unsigned long long a_tasks_deep;  // shared u-partials (one t side each), deep solver
-    unsigned long long b_tasks_deep;  // shared v-partials (one t side each), deep solver
+    unsigned long long a_tasks_deep;  // shared partials (one per t value and u / v), deep solver
+    unsigned long long b_tasks_deep;  // unused (0), kept for the layout
     unsigned long long evals_shared_deep;  // deep box evaluations from shared partials
     unsigned long long checks_pool;   // sum of n over queries finished by the pooled solver
     unsigned long long evals_pool;    // box evaluations executed by the pooled solver
@@ -349,13 +348,6 @@ __device__ __forceinline__ void bsync()
     if (BS == 32) __syncwarp(); else __syncthreads();
 }
 
-__device__ __forceinline__ int warp_min(int v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 __device__ __forceinline__ long long warp_minl(long long v)
 {
 #pragma unroll
@@ -390,25 +382,7 @@ struct Smem {
     unsigned long long run_at[BS];   // a_t of each run of equal t_L
     int ired[BS / 32 + 1];
     long long lred[BS / 32 + 1];
-    unsigned long long first_at;
-    double first_w;
-    int first_term;
-    double cut_w;
 };
-
-template <int BS>
-__device__ __forceinline__ int block_min(int v, Smem<BS> &s)
-{
-    v = warp_min(v);
-    if (BS == 32) return v;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s.ired[warp] = v;
-    __syncthreads();
-    int r = lane < BS / 32 ? s.ired[lane] : BIG;
-    r = warp_min(r);
-    __syncthreads();
-    return r;
-}
 
 template <int BS>
 __device__ __forceinline__ long long block_minl(long long v, Smem<BS> &s)
@@ -2053,7 +2027,7 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
                                               &h->survivors, &h->head_pool, nullptr, 0);
     stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
-    const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared u/v partials
+    const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared partials
     if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
             cudaSuccess ||
