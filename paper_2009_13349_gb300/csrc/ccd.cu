@@ -3,35 +3,44 @@
 //
 // Execution plan of one batch (all launches on the caller's stream, no host
 // synchronisation, no allocation):
-//   1. root_kernel     one thread per query: loads the 192-byte record,
-//                      checks the level-0 box [0,1]^3 (Eq. box, Eq.
-//                      ccd-error).  Queries rejected there, or terminating
-//                      there, are answered; the rest get kappa (Eq. kappas)
-//                      and join the survivor list.
-//   2. solve_kernel<32>   persistent; one warp per survivor query runs the
-//                      level-synchronous form of Algorithm 2 with its frontier
-//                      in a small private slot.  A query whose frontier
-//                      outgrows the slot moves to the overflow list.
-//   3. solve_kernel<512>  persistent; one 512-thread block per overflow query,
-//                      frontier slot sized for 2 m_I boxes (the most any
-//                      level can hold, see solve_query).
+//   1. root_kernel      one thread per query: loads the 192-byte record,
+//                       checks the level-0 box [0,1]^3 (Eq. box, Eq.
+//                       ccd-error).  Queries rejected there, or terminating
+//                       there, are answered; the rest get kappa (Eq. kappas)
+//                       and join the survivor list.
+//   2. pool_kernel      persistent; one warp holds up to 32 survivor queries
+//                       and packs the next boxes of all of them into its
+//                       lanes; a query whose level outgrows its slot (64
+//                       boxes by default) moves to the next list.
+//   3. solve_kernel<32> persistent; one warp per query, frontiers up to 1024
+//                       boxes per level; a query that outgrows it moves to the
+//                       deep list with the level it reached.
+//   4. order_by_level_kernel  sorts the deep list shallowest level first (the
+//                       longest queries first).
+//   5. solve_kernel<256> persistent; one 256-thread block per deep query (two
+//                       resident per SM for VF, three for EE), frontier slot
+//                       sized for 2 m_I boxes (the most any level can hold, see
+//                       solve_query), corners from shared partials.
+// A query that moves on restarts from level 0 in the next stage; its result
+// does not depend on the stage that answers it.
 //
 // Level-synchronous form of Algorithm 2.  Q is ordered by (level, left end
 // of I_t); ties keep insertion order, children inserted left then right.
 // All boxes of one level have the same widths, hence the same split
-// dimension.  A level is therefore an array in Q order: for u/v splits the
-// children of box j are adjacent (left, right); for t splits, each run of
+// dimension.  A level is therefore an array in Q order: for u and v splits
+// the children of box j are adjacent (left, right); for t splits, each run of
 // boxes sharing I_t emits all left children, then all right children.  The
 // check counter of the box at array position i is n_before + i + 1, so the
 // first colliding box, the m_I cut-off and the termination test are decided
-// with block-wide min-reductions, exactly as the sequential loop would.
+// block-wide exactly as the sequential loop would.
 //
 // Boxes are stored as integer numerators (a_t, a_u, a_v) of dyadic
 // endpoints a 2^-k, k <= 53 per dimension, converted to doubles exactly.
-// F is evaluated in the fixed order: positions x0 + (x1 - x0) t first; VF
-// F = (q - u e1) - v e2 with q = p - v1, e1 = v2 - v1, e2 = v3 - v1; EE
-// F = (p1 + u d1) - (p3 + v d2), d1 = p2 - p1, d2 = p4 - p3.  Every add and
-// multiply is an explicit round-to-nearest intrinsic (never contracted).
+// F is evaluated in a fixed fused order: positions fma(x1 - x0, t, x0)
+// first; VF F = fma(-v, e2, fma(-u, e1, q)) with q = p - v1, e1 = v2 - v1,
+// e2 = v3 - v1; EE F = fma(u, d1, p1 - fma(v, d2, p3)), d1 = p2 - p1,
+// d2 = p4 - p3.  Every add, multiply and fused multiply-add is an explicit
+// round-to-nearest intrinsic (nothing else is contracted).
 
 #include "ccd.h"
 
@@ -64,7 +73,7 @@ struct Box {
 struct Header {
     int survivors;   // queries in the survivor list
     int head_small;  // work counter of the small-frontier solver
-    int overflow;    // queries in the overflow list
+    int overflow;    // queries in the deep list (one-warp solver hand-offs)
     int head_deep;   // work counter of the deep solver
     int status;      // CCD_OK or CCD_ERR_CAPACITY
     int fallbacks;   // queries answered by the capacity fallback
@@ -660,7 +669,7 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
     root_query<KIND>(p, i, qp_single(p, i));
 }
 
-// ---- 2./3. per-query level-synchronous solver --------------------------------
+// ---- 3./5. per-query level-synchronous solver (one-warp and deep) ------------
 
 // Runs Algorithm 2 for query qi with BS cooperating threads.  Returns false
 // if a level needed more than `cap` boxes (nothing is written then unless
@@ -1205,10 +1214,10 @@ __device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
 // so that no slot waits long), evaluates them with the same code path, then
 // lets each slot's owner lane apply Algorithm 2's sequential bookkeeping to
 // its boxes in Q order: first colliding box, check limit, termination,
-// children appended in Q order (u/v splits: left then right; t splits: the
+// children appended in Q order (u and v splits: left then right; t splits: the
 // right children of a run of equal t_L wait in a pending list flushed when
-// the run ends).  A level with more children than the slot capacity hands the query
-// to the one-warp solver, which restarts it.
+// the run ends).  A level with more children than the slot capacity hands the
+// query to the one-warp solver, which restarts it.
 struct PoolSlot {
     long long qi, size, pos, n_before;
     unsigned long long if_at, pend_at;
