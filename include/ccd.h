@@ -51,8 +51,7 @@ typedef enum {
 /*
  * Bytes of device workspace that ccd_vf_batch / ccd_ee_batch need for n
  * queries at check limit max_itr with the default number of deep slots (three
- * per SM of the current device: an EE batch runs three deep blocks per SM, a
- * VF batch two).  One deep slot takes 48 * (2 * max_itr + 64)
+ * per SM of the current device: a batch runs three deep blocks per SM).  One deep slot takes 48 * (2 * max_itr + 64)
  * bytes.  A smaller workspace is accepted as long as it holds at least one
  * deep slot; fewer slots only reduce parallelism on queries with very large
  * subdivision frontiers.  Returns 0 on bad arguments or without a device.

@@ -128,8 +128,8 @@ def deep_slot_bytes(max_itr: int) -> int:
     return 2 * (2 * int(max_itr) + 64) * 24
 
 
-# deep-solver slots that ccd_workspace_bytes provides per SM (EE batches run
-# three deep blocks per SM, VF batches two)
+# deep-solver slots that ccd_workspace_bytes provides per SM (a batch runs
+# three deep blocks per SM)
 DEEP_SLOTS_PER_SM = 3
 
 

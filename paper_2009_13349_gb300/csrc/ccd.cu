@@ -17,8 +17,8 @@
 //                       deep list with the level it reached.
 //   4. order_by_level_kernel  sorts the deep list shallowest level first (the
 //                       longest queries first).
-//   5. solve_kernel<256> persistent; one 256-thread block per deep query (two
-//                       resident per SM for VF, three for EE), frontier slot
+//   5. solve_kernel<256> persistent; one 256-thread block per deep query (three
+//                       resident per SM), frontier slot
 //                       sized for 2 m_I boxes (the most any level can hold, see
 //                       solve_query), corners from shared partials.
 // A query that moves on restarts from level 0 in the next stage; its result
@@ -61,9 +61,10 @@ constexpr int POOL_CAP_MAX = 4096;
 constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
                                        // launch takes what the occupancy calculator allows)
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
-constexpr int DEEP_BLOCKS_PER_SM = 2;  // ... and resident blocks (queries) per SM: VF and
-constexpr int DEEP_BLOCKS_PER_SM_EE = 3;  // EE (80 registers without spills); the segmented
-                                        // kernel, which runs both kinds, keeps 2
+constexpr int DEEP_BLOCKS_PER_SM = 3;  // ... and resident blocks (queries) per SM (80
+                                       // registers without spills) ...
+constexpr int SEG_DEEP_BLOCKS_PER_SM = 2;  // ... and for the segmented kernel, which runs
+                                           // both kinds
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
 struct Box {
@@ -904,7 +905,10 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
         if (cu > cm) cm = cu;
         if (cv > cm) cm = cv;
         const int sd = (ct == cm) ? 0 : (cu == cm) ? 1 : 2;
-        const bool can_split = k[sd] < KMAX;
+        // (the deep solver uses selects where the one-warp solver indexes by sd: a
+        // dynamic index there puts k and the child boxes in local memory, which
+        // kept the VF deep solver from three blocks per SM)
+        const bool can_split = (BS > 32 ? (sd == 0 ? k[0] : sd == 1 ? k[1] : k[2]) : k[sd]) < KMAX;
 
         bool found = false;
         unsigned long long if_at = 0;
@@ -1073,8 +1077,16 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 if (valid) {
                     const long long pos = j + carry + pre;
                     Box l = b, r = b;
-                    l.a[sd] = 2 * b.a[sd];
-                    r.a[sd] = 2 * b.a[sd] + 1;
+                    if (BS > 32) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            l.a[d] = d == sd ? 2 * b.a[d] : b.a[d];
+                            r.a[d] = d == sd ? 2 * b.a[d] + 1 : b.a[d];
+                        }
+                    } else {
+                        l.a[sd] = 2 * b.a[sd];
+                        r.a[sd] = 2 * b.a[sd] + 1;
+                    }
                     if (pos < cap) nxt[pos] = l;
                     if (keep_r && pos + 1 < cap) nxt[pos + 1] = r;
                 }
@@ -1102,7 +1114,12 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
         cur = nxt;
         nxt = t;
         size = nchild;
-        k[sd] += 1;
+        if (BS > 32) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) k[d] += d == sd;
+        } else {
+            k[sd] += 1;
+        }
     }
 }
 
@@ -1111,9 +1128,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 // level it reached in out_level when that is not null (one-warp tier only;
 // the deep tier answers it through the capacity fallback).
 template <int KIND, int BS>
-__global__ void __launch_bounds__(BS, BS == 256 ? (KIND == CCD_KIND_EE ? DEEP_BLOCKS_PER_SM_EE
-                                                                    : DEEP_BLOCKS_PER_SM)
-                                              : 1)
+__global__ void __launch_bounds__(BS, BS == 256 ? DEEP_BLOCKS_PER_SM : 1)
     solve_kernel(Params p, int deep, Box *slots, long long cap, const int *list,
                  const int *count, int *head, int *out_list, unsigned char *out_level,
                  int *out_count)
@@ -1540,7 +1555,7 @@ __global__ void __launch_bounds__(ROOT_THREADS)
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS, BS == 256 ? 2 : 1)
+__global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
                      long long cap)
 {
@@ -1972,7 +1987,7 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
     const size_t per = sizeof(Box) * 2 * (size_t)want;
     long long nb = (long long)(room / per);
     if (nb >= 1) {
-        const long long most = (long long)DEEP_BLOCKS_PER_SM_EE * sms;
+        const long long most = (long long)DEEP_BLOCKS_PER_SM * sms;
         L.nb_deep = (int)(nb < most ? nb : most);
         L.cap_deep = want;
     } else {
@@ -2044,8 +2059,7 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return CCD_ERR_CUDA;
     {   // resident deep blocks per SM for this kind
-        const int per_sm = KIND == CCD_KIND_EE ? DEEP_BLOCKS_PER_SM_EE : DEEP_BLOCKS_PER_SM;
-        if (L.nb_deep > per_sm * sms) L.nb_deep = per_sm * sms;
+        if (L.nb_deep > DEEP_BLOCKS_PER_SM * sms) L.nb_deep = DEEP_BLOCKS_PER_SM * sms;
     }
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
@@ -2071,7 +2085,7 @@ size_t ccd_workspace_bytes(int64_t n, int64_t max_itr)
     if (sms <= 0) return 0;
     Layout L = layout_fixed(n, sms);
     return L.off_deep +
-           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM_EE * sms);
+           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM * sms);
 }
 
 ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err, int err_stride,
@@ -2222,7 +2236,7 @@ struct Tuned {
 
 bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
 {
-    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
+    Tuned r{DEEP_THREADS, SEG_DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
     if (t) {
         if (t->deep_threads) r.deep_threads = t->deep_threads;
         if (t->deep_slots) r.deep_slots = t->deep_slots;
