@@ -38,19 +38,23 @@ PAPER_CONTEXT = {
 # FP64 pipe instructions (add, sub, mul or fused multiply-add, one each) of
 # the fixed F expression.  A t-quantity evaluation (one t value: 12 positions
 # fma(dx, t, x0), then VF 9 / EE 6 differences) is shared by a run of boxes
-# with equal t_L; a box evaluated from two t-quantity sets costs, per t and
-# coordinate, VF 2 fma (q - u e1) + 4 fma (- v e2) / EE 2 x (fma + difference)
-# (p1 - (p3 + v d2)) + 4 fma (+ u d1), plus 3 for w(B).
+# with equal t_L.  Per t and coordinate a box has two partials (VF 2 fma
+# q - u e1; EE 2 x (fma + difference) p1 - (p3 + v d2)) and four corners
+# (fma - v e2 / + u d1); the min and max of the four are the two extreme
+# corners, one fma each, so the solvers evaluate 2 of them (the deep
+# solver's per-box fallback evaluates all 4).  Plus 3 for w(B).
 T_OPS = {0: 12 + 9, 1: 12 + 6}
-BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
+BOX_OPS = {0: 2 * 3 * 4 + 3, 1: 2 * 3 * 6 + 3}
+FULL_BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
 # deep solver with shared partials: one partial per (t value, parameter),
 # VF a(t,u) = fma(-u, e1, q) (3), EE c(t,v) = p1 - fma(v, d2, p3) (6); a box
-# then needs only its 8 fused corners (24) and w(B) (3)
+# then needs only its 4 extreme corners (12) and w(B) (3)
 A_OPS = {0: 3, 1: 6}
 B_OPS = {0: 0, 1: 0}
-SHARED_BOX_OPS = 24 + 3
-# the same check evaluated on its own (no sharing): 2 t-quantities + box
-OPS_PER_CHECK = {k: 2 * T_OPS[k] + BOX_OPS[k] for k in (0, 1)}
+SHARED_BOX_OPS = 12 + 3
+# the same check evaluated on its own as the definition reads (no sharing,
+# all 8 corners): 2 t-quantities + box
+OPS_PER_CHECK = {k: 2 * T_OPS[k] + FULL_BOX_OPS[k] for k in (0, 1)}
 
 
 def parse():
@@ -330,7 +334,8 @@ def run_native(args):
         for j, b in enumerate(batches):
             c = counters[j]
             shared = c["evals_shared_deep"] if sfx == "deep" else 0
-            alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * BOX_OPS[b.kind]
+            per_box = (FULL_BOX_OPS if sfx == "deep" else BOX_OPS)[b.kind]   # deep: fallback
+            alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * per_box
                         + shared * SHARED_BOX_OPS)
             if sfx == "deep":
                 alg_ops += c["a_tasks_deep"] * A_OPS[b.kind] + c["b_tasks_deep"] * B_OPS[b.kind]

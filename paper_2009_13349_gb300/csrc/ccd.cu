@@ -232,6 +232,25 @@ __device__ __forceinline__ void t_quantities_axis(const Query &Q, double t, int 
     }
 }
 
+// Keys of the min and max over the four corners fma(x, g, p) of one axis at
+// one t, x in {x_lo, x_hi} (x_lo < x_hi) and p in {p0, p1}.  The exact value
+// x g + p is non-decreasing in p, and in x when g > 0 (non-increasing when g
+// < 0; for g = +-0 both x give the same result, as x_lo and x_hi have one
+// sign), and rounding is monotone, so the extreme corners are fma at the
+// smaller p with the x that makes x g smallest, and at the larger p with the
+// other x.  Two fmas give the same bits as the min and max of all four, in
+// key order (-0 before +0) too: for a fixed x the result is key-monotone in
+// p, including zero results.  (Finite g and p; no NaN arises from them.)
+__device__ __forceinline__ void corner_range(double x_lo, double x_hi, double g, double p0,
+                                             double p1, long long &lo, long long &hi)
+{
+    const bool sw = dkey(p1) < dkey(p0);
+    const double pmin = sw ? p1 : p0, pmax = sw ? p0 : p1;
+    const bool neg = __double_as_longlong(g) < 0;   // sign bit
+    lo = dkey(dfma(neg ? x_hi : x_lo, g, pmin));
+    hi = dkey(dfma(neg ? x_lo : x_hi, g, pmax));
+}
+
 // B_F(I) from the t-quantities of t_L (TL) and t_R (TR): per-axis integer
 // keys of the min and max over the 8 corners.
 template <int KIND>
@@ -244,21 +263,16 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
         const double *T = side ? TR : TL;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double f0, f1, f2, f3;
-            if (KIND == CCD_KIND_VF) {
+            long long lo, hi;
+            if (KIND == CCD_KIND_VF) {   // F = fma(-v, e2, fma(-u, e1, q))
                 const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
                 const double al = dfma(-ul, e1, q), ar = dfma(-ur, e1, q);
-                f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
-                f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
-            } else {
+                corner_range(-vr, -vl, e2, al, ar, lo, hi);
+            } else {                     // F = fma(u, d1, p1 - fma(v, d2, p3))
                 const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
                 const double cl = dsub(a, dfma(vl, d2, b)), cr = dsub(a, dfma(vr, d2, b));
-                f0 = dfma(ul, d1, cl); f1 = dfma(ul, d1, cr);
-                f2 = dfma(ur, d1, cl); f3 = dfma(ur, d1, cr);
+                corner_range(ul, ur, d1, cl, cr, lo, hi);
             }
-            const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
-            const long long lo = min(min(k0, k1), min(k2, k3));
-            const long long hi = max(max(k0, k1), max(k2, k3));
             if (side == 0) { km[c] = lo; kM[c] = hi; }
             else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
         }
@@ -266,6 +280,9 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
 }
 
 // One t side of corners_keys: accumulates the keys of the 4 corners at one t.
+// (Only the deep solver's per-box fallback uses it; it evaluates all four
+// corners, which keeps that kernel within its register budget, and gives the
+// same keys as corner_range.)
 template <int KIND>
 __device__ __forceinline__ void corners_keys_side(const double *T, double ul, double ur,
                                                   double vl, double vr, bool first,
@@ -832,6 +849,12 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     }
     ptasks += (unsigned long long)NP;
     shared_evals += (unsigned long long)nvalid;
+    // this box's partial ids (final since the barrier above), loaded ahead of
+    // the partial tasks so that the corners need one shared load, not two
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sk[j] = sh.id[sk[j]];
+    }
     for (int task = tid; task < NP; task += BS) {
         const unsigned long long key = sh.key_by_id[task];
         const double x = dyadic(key & SH_VAL_MASK, k[PD]);
@@ -847,19 +870,16 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         const double yl = dyadic(b.a[FD], k[FD]), yr = dyadic(b.a[FD] + 1, k[FD]);
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const int i0 = sh.id[sk[2 * side]], i1 = sh.id[sk[2 * side + 1]];
+            const int i0 = sk[2 * side], i1 = sk[2 * side + 1];
             const double *T = sh.tq[tl + side];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double p0 = sh.part[i0][c], p1 = sh.part[i1][c];
                 // VF: fma(-v, e2, a); EE: fma(u, d1, c)
                 const double g = KIND == CCD_KIND_VF ? T[6 + c] : T[3 + c];
-                const double ml = KIND == CCD_KIND_VF ? -yl : yl, mr = KIND == CCD_KIND_VF ? -yr : yr;
-                const double f0 = dfma(ml, g, p0), f1 = dfma(mr, g, p0);
-                const double f2 = dfma(ml, g, p1), f3 = dfma(mr, g, p1);
-                const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
-                const long long lo = min(min(k0, k1), min(k2, k3));
-                const long long hi = max(max(k0, k1), max(k2, k3));
+                long long lo, hi;
+                if (KIND == CCD_KIND_VF) corner_range(-yr, -yl, g, p0, p1, lo, hi);
+                else corner_range(yl, yr, g, p0, p1, lo, hi);
                 if (side == 0) { km[c] = lo; kM[c] = hi; }
                 else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
             }
