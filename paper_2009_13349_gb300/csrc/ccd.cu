@@ -125,6 +125,14 @@ __device__ __forceinline__ double pow2neg(int k)
 }
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+// 2^-k x, exact: by exponent arithmetic while the result stays normal
+__device__ __forceinline__ double scale2neg(double x, int k)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    return (e > k && e < 0x7ff) ? __longlong_as_double(b - ((long long)k << 52))
+                                : __dmul_rn(pow2neg(k), x);
+}
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -241,14 +249,20 @@ __device__ __forceinline__ void t_quantities_axis(const Query &Q, double t, int 
 // other x.  Two fmas give the same bits as the min and max of all four, in
 // key order (-0 before +0) too: for a fixed x the result is key-monotone in
 // p, including zero results.  (Finite g and p; no NaN arises from them.)
-__device__ __forceinline__ void corner_range(double x_lo, double x_hi, double g, double p0,
+//
+// NEG: x = -y for y in {y_lo, y_hi} (VF's -v), else x = y (EE's u); the
+// negation goes into the fma's operand, fma(-y, g, p).
+template <bool NEG>
+__device__ __forceinline__ void corner_range(double y_lo, double y_hi, double g, double p0,
                                              double p1, long long &lo, long long &hi)
 {
     const bool sw = dkey(p1) < dkey(p0);
     const double pmin = sw ? p1 : p0, pmax = sw ? p0 : p1;
-    const bool neg = __double_as_longlong(g) < 0;   // sign bit
-    lo = dkey(dfma(neg ? x_hi : x_lo, g, pmin));
-    hi = dkey(dfma(neg ? x_lo : x_hi, g, pmax));
+    // x g smallest: x_lo = (NEG ? -y_hi : y_lo) when g's sign bit is clear
+    const bool hi_y = (__double_as_longlong(g) < 0) != NEG;
+    const double ymin = hi_y ? y_hi : y_lo, ymax = hi_y ? y_lo : y_hi;
+    lo = dkey(dfma(NEG ? -ymin : ymin, g, pmin));
+    hi = dkey(dfma(NEG ? -ymax : ymax, g, pmax));
 }
 
 // B_F(I) from the t-quantities of t_L (TL) and t_R (TR): per-axis integer
@@ -267,11 +281,11 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
             if (KIND == CCD_KIND_VF) {   // F = fma(-v, e2, fma(-u, e1, q))
                 const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
                 const double al = dfma(-ul, e1, q), ar = dfma(-ur, e1, q);
-                corner_range(-vr, -vl, e2, al, ar, lo, hi);
+                corner_range<true>(vl, vr, e2, al, ar, lo, hi);
             } else {                     // F = fma(u, d1, p1 - fma(v, d2, p3))
                 const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
                 const double cl = dsub(a, dfma(vl, d2, b)), cr = dsub(a, dfma(vr, d2, b));
-                corner_range(ul, ur, d1, cl, cr, lo, hi);
+                corner_range<false>(ul, ur, d1, cl, cr, lo, hi);
             }
             if (side == 0) { km[c] = lo; kM[c] = hi; }
             else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
@@ -878,8 +892,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
                 // VF: fma(-v, e2, a); EE: fma(u, d1, c)
                 const double g = KIND == CCD_KIND_VF ? T[6 + c] : T[3 + c];
                 long long lo, hi;
-                if (KIND == CCD_KIND_VF) corner_range(-yr, -yl, g, p0, p1, lo, hi);
-                else corner_range(yl, yr, g, p0, p1, lo, hi);
+                corner_range<KIND == CCD_KIND_VF>(yl, yr, g, p0, p1, lo, hi);
                 if (side == 0) { km[c] = lo; kM[c] = hi; }
                 else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
             }
@@ -918,9 +931,9 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 
     for (;;) {
         // split(): c_d = w(I_d) kappa_d, ties t > u > v.  Same for the level.
-        const double ct = dmul(pow2neg(k[0]), kap[0]);
-        const double cu = dmul(pow2neg(k[1]), kap[1]);
-        const double cv = dmul(pow2neg(k[2]), kap[2]);
+        const double ct = scale2neg(kap[0], k[0]);
+        const double cu = scale2neg(kap[1], k[1]);
+        const double cv = scale2neg(kap[2], k[2]);
         double cm = ct;
         if (cu > cm) cm = cu;
         if (cv > cm) cm = cv;
@@ -1283,9 +1296,9 @@ struct PoolShared {
 
 __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[3])
 {
-    const double ct = dmul(pow2neg(S.k[0]), kap[0]);
-    const double cu = dmul(pow2neg(S.k[1]), kap[1]);
-    const double cv = dmul(pow2neg(S.k[2]), kap[2]);
+    const double ct = scale2neg(kap[0], S.k[0]);
+    const double cu = scale2neg(kap[1], S.k[1]);
+    const double cv = scale2neg(kap[2], S.k[2]);
     double cm = ct;
     if (cu > cm) cm = cu;
     if (cv > cm) cm = cv;
