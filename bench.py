@@ -41,8 +41,8 @@ PAPER_CONTEXT = {
 # with equal t_L.  Per t and coordinate a box has two partials (VF 2 fma
 # q - u e1; EE 2 x (fma + difference) p1 - (p3 + v d2)) and four corners
 # (fma - v e2 / + u d1); the min and max of the four are the two extreme
-# corners, one fma each, so the solvers evaluate 2 of them (the deep
-# solver's per-box fallback evaluates all 4).  Plus 3 for w(B).
+# corners, one fma each, so the solvers evaluate 2 of them.  Plus 3 for
+# w(B).  (FULL_BOX_OPS: all four corners, as the definition reads.)
 T_OPS = {0: 12 + 9, 1: 12 + 6}
 BOX_OPS = {0: 2 * 3 * 4 + 3, 1: 2 * 3 * 6 + 3}
 FULL_BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
@@ -349,7 +349,7 @@ def run_native(args):
         for j, b in enumerate(batches):
             c = counters[j]
             shared = c["evals_shared_deep"] if sfx == "deep" else 0
-            per_box = (FULL_BOX_OPS if sfx == "deep" else BOX_OPS)[b.kind]   # deep: fallback
+            per_box = BOX_OPS[b.kind]   # deep: every box goes through the shared partials
             alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * per_box
                         + shared * SHARED_BOX_OPS)
             if sfx == "deep":

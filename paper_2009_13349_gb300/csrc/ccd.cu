@@ -293,37 +293,6 @@ __device__ __forceinline__ void corners_keys(const double *TL, const double *TR,
     }
 }
 
-// One t side of corners_keys: accumulates the keys of the 4 corners at one t.
-// (Only the deep solver's per-box fallback uses it; it evaluates all four
-// corners, which keeps that kernel within its register budget, and gives the
-// same keys as corner_range.)
-template <int KIND>
-__device__ __forceinline__ void corners_keys_side(const double *T, double ul, double ur,
-                                                  double vl, double vr, bool first,
-                                                  long long (&km)[3], long long (&kM)[3])
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double f0, f1, f2, f3;
-        if (KIND == CCD_KIND_VF) {
-            const double q = T[c], e1 = T[3 + c], e2 = T[6 + c];
-            const double al = dfma(-ul, e1, q), ar = dfma(-ur, e1, q);
-            f0 = dfma(-vl, e2, al); f1 = dfma(-vr, e2, al);
-            f2 = dfma(-vl, e2, ar); f3 = dfma(-vr, e2, ar);
-        } else {
-            const double a = T[c], d1 = T[3 + c], b = T[6 + c], d2 = T[9 + c];
-            const double cl = dsub(a, dfma(vl, d2, b)), cr = dsub(a, dfma(vr, d2, b));
-            f0 = dfma(ul, d1, cl); f1 = dfma(ul, d1, cr);
-            f2 = dfma(ur, d1, cl); f3 = dfma(ur, d1, cr);
-        }
-        const long long k0 = dkey(f0), k1 = dkey(f1), k2 = dkey(f2), k3 = dkey(f3);
-        const long long lo = min(min(k0, k1), min(k2, k3));
-        const long long hi = max(max(k0, k1), max(k2, k3));
-        if (first) { km[c] = lo; kM[c] = hi; }
-        else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
-    }
-}
-
 // The box test of Algorithm 2 on integer keys (Sec. 5.1 enlargement by ms).
 __device__ __forceinline__ void box_test_keys(const long long (&km)[3], const long long (&kM)[3],
                                               const Thresholds &T, double ms, bool &hit,
@@ -744,10 +713,15 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 // has that id + 1).  Distinct keys are found with a shared-memory hash
 // table; dense partial ids come from a second block scan; tasks are packed
 // into consecutive lanes.  A chunk with more than SH_RUN_CAP runs or
-// SH_ENTRY_CAP distinct partials is evaluated per box instead.
-constexpr int SH_RUN_CAP = 96;
+// SH_ENTRY_CAP distinct partials is evaluated as sub-chunks of SH_SUB boxes,
+// which always fit (a box adds at most one run, two t values and four
+// partials); every box gets the same rounded operations either way.
+constexpr int SH_RUN_CAP = 128;
 constexpr int SH_TV_CAP = 2 * SH_RUN_CAP;           // distinct t values per chunk
-constexpr int SH_ENTRY_CAP = 640;                   // partials (one t value each)
+constexpr int SH_ENTRY_CAP = 512;                   // partials (one t value each)
+constexpr int SH_SUB = 128;
+static_assert(SH_SUB <= SH_RUN_CAP && 2 * SH_SUB <= SH_TV_CAP && 4 * SH_SUB <= SH_ENTRY_CAP,
+              "a sub-chunk always fits the tables");
 constexpr int SH_SLOTS = 2048;                      // hash slots, power of two
 constexpr unsigned long long SH_EMPTY = ~0ull;
 constexpr unsigned long long SH_VAL_MASK = (1ull << 54) - 1;
@@ -774,29 +748,15 @@ __device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long 
     }
 }
 
-// Per-box evaluation with private t-quantities (the fallback path).
-template <int KIND>
-__device__ __forceinline__ void eval_box_private(const Query &Q, const QP &q,
-                                                 const Thresholds &TH, const int (&k)[3],
-                                                 const Box &b, BoxTest &bt)
-{
-    constexpr int W = TWidth<KIND>::W;
-    const double ul = dyadic(b.a[1], k[1]), ur = dyadic(b.a[1] + 1, k[1]);
-    const double vl = dyadic(b.a[2], k[2]), vr = dyadic(b.a[2] + 1, k[2]);
-    long long km[3], kM[3];
-    double T[W];
-    t_quantities<KIND>(Q, dmul(q.t_max, dyadic(b.a[0], k[0])), T);
-    corners_keys_side<KIND>(T, ul, ur, vl, vr, true, km, kM);
-    t_quantities<KIND>(Q, dmul(q.t_max, dyadic(b.a[0] + 1, k[0])), T);
-    corners_keys_side<KIND>(T, ul, ur, vl, vr, false, km, kM);
-    box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
-}
-
-// One chunk (one box per thread) through shared partials.
+// One chunk, or one sub-chunk, through shared partials: threads v_begin ..
+// v_end - 1 hold its boxes (`valid`, one box per thread).
+// Returns false, having set nothing, when the chunk exceeds a table (the
+// caller then evaluates it as sub-chunks).
 template <int KIND, int BS>
-__device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
+__device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
                                                   const Thresholds &TH, const int (&k)[3],
-                                                  bool valid, const Box &b, long long nvalid,
+                                                  bool valid, const Box &b, int v_begin,
+                                                  int v_end,
                                                   Smem<BS> &s, SharedUV &sh, BoxTest &bt,
                                                   unsigned long long &tqs,
                                                   unsigned long long &ptasks,
@@ -809,19 +769,16 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
     s.at[tid] = valid ? b.a[0] : ~0ull;
     for (int j = tid; j < SH_SLOTS; j += BS) sh.key[j] = SH_EMPTY;
     __syncthreads();
-    // runs of equal t_L, and gaps between consecutive runs' t values
+    // runs of equal t_L, and gaps between consecutive runs' t values (a box
+    // outside the (sub-)chunk has a_t = ~0 here)
     const bool start = valid && (tid == 0 || s.at[tid - 1] != b.a[0]);
-    const bool gap = start && tid > 0 && s.at[tid - 1] + 1 != b.a[0];
-    const bool open_r = valid && (tid + 1 >= nvalid || (s.at[tid + 1] != b.a[0] &&
+    const bool gap = start && tid > 0 && s.at[tid - 1] != ~0ull && s.at[tid - 1] + 1 != b.a[0];
+    const bool open_r = valid && (tid + 1 >= v_end || (s.at[tid + 1] != b.a[0] &&
                                                          s.at[tid + 1] != b.a[0] + 1));
     int tot;
     const int pk = block_scan_1sync<BS>((start ? 1 : 0) | ((gap ? 1 : 0) << 16), &tot, s.scan_a);
     const int nrun = tot & 0xffff, ntv = nrun + (tot >> 16) + 1;
-    if (nrun > SH_RUN_CAP) {                       // block-uniform
-        tqs += 2 * (unsigned long long)nvalid;
-        if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
-        return;
-    }
+    if (nrun > SH_RUN_CAP) return false;           // block-uniform
     const int tl = (pk & 0xffff) + (start ? 0 : -1) + (pk >> 16) + (gap ? 1 : 0);   // id of t_L
     if (start) s.run_at[tl] = b.a[0];
     if (open_r) s.run_at[tl + 1] = b.a[0] + 1;     // t_R not shared with the next run
@@ -856,13 +813,9 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         }
     }
     __syncthreads();
-    if (!share) {
-        tqs += 2 * (unsigned long long)nvalid;
-        if (valid) eval_box_private<KIND>(Q, q, TH, k, b, bt);
-        return;
-    }
+    if (!share) return false;
     ptasks += (unsigned long long)NP;
-    shared_evals += (unsigned long long)nvalid;
+    shared_evals += (unsigned long long)(v_end - v_begin);
     // this box's partial ids (final since the barrier above), loaded ahead of
     // the partial tasks so that the corners need one shared load, not two
     if (valid) {
@@ -899,6 +852,7 @@ __device__ __forceinline__ void eval_chunk_shared(const Query &Q, const QP &q,
         }
         box_test_keys(km, kM, TH, q.ms, bt.hit, bt.term, bt.w);
     }
+    return true;
 }
 
 template <int KIND, int BS>
@@ -954,8 +908,19 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             BoxTest bt{false, false, 0.0};
             if (valid) b = cur[i];
             if (BS > 32) {
-                eval_chunk_shared<KIND, BS>(Q, q, TH, k, valid, b, min((long long)BS, size - base),
-                                            s, *(SharedUV *)tq, bt, tqs, atasks, shared_evals);
+                // the whole chunk, else its sub-chunks in turn (block-uniform;
+                // a sub-chunk always fits, so each pass makes progress)
+                const int nv = (int)min((long long)BS, size - base);
+                int h = 0, he = nv;
+                for (;;) {
+                    const bool done = eval_chunk_shared<KIND, BS>(
+                        Q, q, TH, k, valid && tid >= h && tid < he, b, h, he, s, *(SharedUV *)tq,
+                        bt, tqs, atasks, shared_evals);
+                    if (done && he >= nv) break;
+                    if (done) h = he;
+                    else if (he - h <= SH_SUB) break;   // unreachable: see SH_SUB
+                    he = min(nv, h + SH_SUB);
+                }
             } else {
             // Boxes are in Q order, so equal t_L form contiguous runs: the
             // t-quantities at t_L and t_R are computed once per run.
@@ -2091,8 +2056,14 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
         cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return CCD_ERR_CUDA;
-    {   // resident deep blocks per SM for this kind
-        if (L.nb_deep > DEEP_BLOCKS_PER_SM * sms) L.nb_deep = DEEP_BLOCKS_PER_SM * sms;
+    {   // resident deep blocks per SM: the persistent grid must fit at once
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<KIND, DEEP_THREADS>,
+                                                          DEEP_THREADS, tq_deep) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        if (per_sm > DEEP_BLOCKS_PER_SM) per_sm = DEEP_BLOCKS_PER_SM;
+        if (L.nb_deep > per_sm * sms) L.nb_deep = per_sm * sms;
     }
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
