@@ -50,7 +50,6 @@ FULL_BOX_OPS = {0: 2 * 3 * 6 + 3, 1: 2 * 3 * 8 + 3}
 # VF a(t,u) = fma(-u, e1, q) (3), EE c(t,v) = p1 - fma(v, d2, p3) (6); a box
 # then needs only its 4 extreme corners (12) and w(B) (3)
 A_OPS = {0: 3, 1: 6}
-B_OPS = {0: 0, 1: 0}
 SHARED_BOX_OPS = 12 + 3
 # the same check evaluated on its own as the definition reads (no sharing,
 # all 8 corners): 2 t-quantities + box
@@ -353,7 +352,7 @@ def run_native(args):
             alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * per_box
                         + shared * SHARED_BOX_OPS)
             if sfx == "deep":
-                alg_ops += c["a_tasks_deep"] * A_OPS[b.kind] + c["b_tasks_deep"] * B_OPS[b.kind]
+                alg_ops += c["a_tasks_deep"] * A_OPS[b.kind]
         naive = sum(counters[j]["checks_" + sfx] * OPS_PER_CHECK[b.kind]
                     for j, b in enumerate(batches))
     achieved = alg_ops / (per_kernel[top] * 1e-3)

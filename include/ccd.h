@@ -139,9 +139,10 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * [8] t-quantity evaluations (positions and edge vectors at one t, shared by
  * a run of boxes with equal t_L) by the small-frontier solver, [9] the same
  * for the deep solver, [10] shared partials computed by the deep solver (one
- * per t value and parameter value: u for VF, v for EE), [11] always 0 (kept
- * for the layout), [12] deep box evaluations
- * that used the shared partials, [13] queries the pooled solver handed to
+ * per t value and parameter value: u for VF, v for EE), [11] deep chunks
+ * that exceeded the shared tables and were evaluated as sub-chunks of 128
+ * boxes, [12] deep box evaluations that used the shared partials (all of
+ * them), [13] queries the pooled solver handed to
  * the one-warp solver, [14] sum of check counts n of queries finished by
  * the pooled solver, [15] box evaluations executed by the pooled solver
  * (each computes its own t-quantities at t_L and t_R).  The small-frontier

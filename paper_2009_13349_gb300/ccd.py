@@ -212,7 +212,7 @@ def workspace_status(ws: torch.Tensor, stream=None):
 
 COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
                  "evals_small", "evals_deep", "status", "tq_small", "tq_deep", "a_tasks_deep",
-                 "b_tasks_deep", "evals_shared_deep", "mid_queries", "checks_pool",
+                 "split_chunks_deep", "evals_shared_deep", "mid_queries", "checks_pool",
                  "evals_pool")
 
 

@@ -87,7 +87,7 @@ struct Header {
     unsigned long long tq_small;      // t-quantity evaluations by the small solver
     unsigned long long tq_deep;       // t-quantity evaluations by the deep solver
     unsigned long long a_tasks_deep;  // shared partials (one per t value and u / v), deep solver
-    unsigned long long b_tasks_deep;  // unused (0), kept for the layout
+    unsigned long long split_chunks_deep;  // deep chunks evaluated as sub-chunks
     unsigned long long evals_shared_deep;  // deep box evaluations from shared partials
     unsigned long long checks_pool;   // sum of n over queries finished by the pooled solver
     unsigned long long evals_pool;    // box evaluations executed by the pooled solver
@@ -683,15 +683,15 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
 __device__ __forceinline__ void count_done(const Params &p, bool deep, long long n,
                                            unsigned long long evals, unsigned long long tqs,
                                            unsigned long long atasks = 0,
-                                           unsigned long long btasks = 0,
+                                           unsigned long long split_chunks = 0,
                                            unsigned long long shared_evals = 0)
 {
     atomicAdd(deep ? &p.hdr->checks_deep : &p.hdr->checks_small, (unsigned long long)n);
     atomicAdd(deep ? &p.hdr->evals_deep : &p.hdr->evals_small, evals);
     atomicAdd(deep ? &p.hdr->tq_deep : &p.hdr->tq_small, tqs);
-    if (atasks | btasks | shared_evals) {
+    if (atasks | split_chunks | shared_evals) {
         atomicAdd(&p.hdr->a_tasks_deep, atasks);
-        atomicAdd(&p.hdr->b_tasks_deep, btasks);
+        atomicAdd(&p.hdr->split_chunks_deep, split_chunks);
         atomicAdd(&p.hdr->evals_shared_deep, shared_evals);
     }
 }
@@ -863,7 +863,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
     unsigned long long tqs = 0;     // t-quantity evaluations (thread 0's tally)
-    unsigned long long atasks = 0, btasks = 0, shared_evals = 0;
+    unsigned long long atasks = 0, split_chunks = 0, shared_evals = 0;
     Query &Q = s.query;             // shared: only the per-run tasks read it
     if (tid < 12) {
         const double a = __ldg(p.verts + (size_t)tid * p.n + qi);
@@ -919,6 +919,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     if (done && he >= nv) break;
                     if (done) h = he;
                     else if (he - h <= SH_SUB) break;   // unreachable: see SH_SUB
+                    else ++split_chunks;
                     he = min(nv, h + SH_SUB);
                 }
             } else {
@@ -985,7 +986,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                         if (tid == 0) {
                             write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w,
                                          nfc);
-                            count_done(p, fallback, nfc, evals, tqs, atasks, btasks,
+                            count_done(p, fallback, nfc, evals, tqs, atasks, split_chunks,
                                        shared_evals);
                         }
                         return true;
@@ -996,7 +997,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     if (tid == 0) {
                         write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])),
                                      s.dec[wc].w_cut, ncut);
-                        count_done(p, fallback, ncut, evals, tqs, atasks, btasks, shared_evals);
+                        count_done(p, fallback, ncut, evals, tqs, atasks, split_chunks, shared_evals);
                     }
                     return true;
                 }
@@ -1010,7 +1011,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
-                count_done(p, fallback, n_before + size, evals, tqs, atasks, btasks, shared_evals);
+                count_done(p, fallback, n_before + size, evals, tqs, atasks, split_chunks, shared_evals);
             }
             return true;
         }
@@ -1103,7 +1104,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
-                count_done(p, true, n_before, evals, tqs, atasks, btasks, shared_evals);
+                count_done(p, true, n_before, evals, tqs, atasks, split_chunks, shared_evals);
             }
             return true;
         }
@@ -2170,7 +2171,7 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[16], v
     counters[8] = (int64_t)h.tq_small;
     counters[9] = (int64_t)h.tq_deep;
     counters[10] = (int64_t)h.a_tasks_deep;
-    counters[11] = (int64_t)h.b_tasks_deep;
+    counters[11] = (int64_t)h.split_chunks_deep;
     counters[12] = (int64_t)h.evals_shared_deep;
     counters[13] = h.mid;
     counters[14] = (int64_t)h.checks_pool;

@@ -72,7 +72,9 @@ def test_multi_equals_single_calls_and_oracle(ccd):
         ref = _out(ccd.batch(kinds[s], vs, e, ms=ms[s], delta=delta[s], max_itr=int(max_itr[s])))
         _eq([x[o:o + c] for x in got], ref)
         idx = rng.choice(c, min(c, 300), replace=False)
-        orc = oracle.ccd_batch(kinds[s], verts[o:o + c][idx], seg["err"][s], ms=ms[s],
+        oe = oracle.err_from_bounds(kinds[s], verts[o:o + c], ms_nonzero=ms[s] > 0)
+        assert np.array_equal(seg["err"][s], oe)
+        orc = oracle.ccd_batch(kinds[s], verts[o:o + c][idx], oe, ms=ms[s],
                                delta=delta[s], max_itr=int(max_itr[s]), nthreads=NT)
         _eq([x[o:o + c][idx] for x in got], orc)
 
@@ -168,7 +170,9 @@ def test_shortened_interval_matches_oracle(ccd):
     got = _out(ccd.multi_batch(v, sd, 1_000_000))
     for s in range(len(counts)):
         o, c = int(seg["offset"][s]), int(seg["count"][s])
-        ref = oracle.ccd_batch(kinds[s], verts[o:o + c], seg["err"][s], ms=mss[s], delta=1e-6,
+        oe = oracle.err_from_bounds(kinds[s], verts[o:o + c], ms_nonzero=mss[s] > 0)
+        assert np.array_equal(seg["err"][s], oe)
+        ref = oracle.ccd_batch(kinds[s], verts[o:o + c], oe, ms=mss[s], delta=1e-6,
                                max_itr=1_000_000, nthreads=NT, t_max=tmaxes[s])
         _eq([x[o:o + c] for x in got], ref)
         hit = ref[0] == 1

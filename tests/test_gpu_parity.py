@@ -29,16 +29,18 @@ def ccd():
 
 def gpu_run(ccd, kind, verts, ms=0.0, delta=1e-6, max_itr=10**6, per_query=False, ws=None,
             err=None):
+    """The CUDA batch on the oracle's eps (the GPU's own eps is checked bit
+    for bit in test_err_from_bounds_bit_exact); returns its outputs and that
+    eps, for the oracle run."""
     v = ccd.to_soa(verts)
     if err is None:
-        e = ccd.err_from_bounds(kind, v, ms_nonzero=ms > 0, per_query=per_query)
-    else:
-        e = torch.as_tensor(err, dtype=torch.float64, device="cuda").contiguous()
+        err = oracle.err_from_bounds(kind, verts, ms_nonzero=ms > 0, per_query=per_query)
+    e = torch.as_tensor(err, dtype=torch.float64, device="cuda").contiguous()
     r = ccd.batch(kind, v, e, ms=ms, delta=delta, max_itr=max_itr, ws=ws)
     torch.cuda.synchronize()
     out = (r.collides.cpu().numpy(), r.toi.cpu().numpy(), r.out_tol.cpu().numpy(),
            r.checks.cpu().numpy())
-    return out, e.cpu().numpy()
+    return out, np.asarray(err, dtype=np.float64)
 
 
 def oracle_run(kind, verts, err, ms=0.0, delta=1e-6, max_itr=10**6):
