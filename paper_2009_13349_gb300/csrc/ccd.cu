@@ -18,9 +18,11 @@
 //   4. order_by_level_kernel  sorts the deep list shallowest level first (the
 //                       longest queries first).
 //   5. solve_kernel<256> persistent; one 256-thread block per deep query (three
-//                       resident per SM), frontier slot
-//                       sized for 2 m_I boxes (the most any level can hold, see
-//                       solve_query), corners from shared partials.
+//                       resident per SM), frontier slot sized for 2 m_I boxes
+//                       (the most any level can hold, see solve_query); a
+//                       chunk of 256 boxes shares its t-quantities and partials
+//                       (a chunk too varied for the tables goes as sub-chunks
+//                       of 128 boxes).
 // A query that moves on restarts from level 0 in the next stage; its result
 // does not depend on the stage that answers it.
 //
@@ -40,7 +42,9 @@
 // first; VF F = fma(-v, e2, fma(-u, e1, q)) with q = p - v1, e1 = v2 - v1,
 // e2 = v3 - v1; EE F = fma(u, d1, p1 - fma(v, d2, p3)), d1 = p2 - p1,
 // d2 = p4 - p3.  Every add, multiply and fused multiply-add is an explicit
-// round-to-nearest intrinsic (nothing else is contracted).
+// round-to-nearest intrinsic (nothing else is contracted).  Per axis and t
+// value, the minimum and maximum of B_F's corners are taken from the two
+// extreme corners (corner_range), which give the same bits as all four.
 
 #include "ccd.h"
 
