@@ -68,6 +68,15 @@ MUTANTS = [
      [("const double det = a11 * a22 - a12 * a21;", "const double det = a11 * a22 + a12 * a21;")]),
     ("scene bound without the floor of 1",
      [("double g[3] = {1.0, 1.0, 1.0};", "double g[3] = {0.0, 0.0, 0.0};")]),
+    ("kappa_u without its factor 3", [("kappa[1] = 3.0 * ku;", "kappa[1] = ku;")]),
+    ("kappa_u measured along t",
+     [("double du = fabs(F[i][0][j][c] - F[i][1][j][c]);",
+       "double du = fabs(F[0][i][j][c] - F[1][i][j][c]);")]),
+    ("per-query bound carried over from the previous query",
+     [("        if (per_query) g[0] = g[1] = g[2] = 1.0;\n", "")]),
+    ("scene eps with the bound squared",
+     [("            err_out[c] = K * ((g[c] * g[c]) * g[c]);",
+       "            err_out[c] = K * (g[c] * g[c]);")]),
 ]
 
 
