@@ -246,3 +246,26 @@ def test_step_over_a_mixed_set_takes_the_earliest_candidate():
     assert r["d_i"] == h_ee
     assert r["alpha"] <= min(a_vf["alpha"], a_ee["alpha"]) + 1e-12
     assert r["alpha"] >= min(a_vf["alpha"], a_ee["alpha"]) - 1e-5
+
+
+def test_distance_and_tolerance_reductions_over_the_set():
+    """Over a candidate set (Algorithm 4), d_i is the smallest distance of
+    the set, and one pass leaves delta_i = max(delta, the tolerances it
+    reached).  Three points fall onto the triangle from different heights;
+    the distances are checked against exact rational ones, and with a small
+    check limit the reached tolerances exceed delta and differ, so the
+    maximum is the only reduction that gives delta_i."""
+    delta, max_itr = 1e-6, 40
+    heights = [2.0**-5, 2.0**-7, 2.0**-6]
+    vf = np.stack([falling_point(h, -h, xy=(0.2 + 0.1 * i, 0.25)) for i, h in enumerate(heights)])
+    d_exact = [float(exact.linf_distance(VF, q)) for q in vf]
+    assert d_exact == heights
+    r = line_search_ccd(vf, np.zeros((0, 24)), p=0.5, delta=delta, max_itr=max_itr,
+                        max_passes=1)
+    assert r["d_i"] == min(d_exact)
+    eps = oracle.err_from_bounds(VF, vf, ms_nonzero=True)
+    col, toi, tol, chk = oracle.ccd_batch(VF, vf, eps, ms=r["d"], delta=delta, max_itr=max_itr)
+    assert np.all(col == 1) and np.all(chk >= max_itr)      # every query cut by the limit
+    assert tol.min() < tol.max() and tol.min() > delta
+    assert r["delta_i"] == max(delta, float(tol.max()))
+    assert r["alpha"] == float(toi.min())

@@ -1,15 +1,20 @@
 """The oracle's pins are not circular: each plausible mistake planted in a
-copy of the oracle's C source makes the pin suite fail.
+copy of the oracle makes the pin suite fail.
 
-Every mutant below is a one-spot edit of ``oracle/ccd_oracle.c`` (a dropped
-term, a wrong sign or index, a swapped comparison or constant, a wrong tie
-order ...).  The test builds each mutant into its own library and runs the
-CPU pin files against it (``CCD_ORACLE_LIB``); a mutant that passes them all
-would be a mistake the pins cannot see.  An unmodified copy built the same
-way must pass, which checks the harness itself.
+Every mutant below is a one-spot edit (a dropped term, a wrong sign or
+index, a swapped comparison or constant, a wrong tie order ...) of
+``oracle/ccd_oracle.c`` or of one of the oracle's Python modules (the active
+set of Algorithm 3, the line-search step of Algorithm 4).  A C mutant is
+built into its own library and the CPU pin files run against it
+(``CCD_ORACLE_LIB``); a Python mutant goes into a copy of the ``oracle``
+package in a scratch directory, with copies of the pin files, and the pins
+run there.  A mutant that passes them all would be a mistake the pins cannot
+see.  An unmodified copy handled the same way must pass, which checks each
+harness itself.
 """
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -98,6 +103,80 @@ def _run_pins(lib):
                         "-m", "not gpu", *PINS], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
     return r.returncode
+
+
+# (module under oracle/, name, substitutions)
+PY_MUTANTS = [
+    ("activeset.py", "swept boxes overlap only strictly",
+     [("return np.all((lo_a <= hi_b) & (lo_b <= hi_a), axis=-1)",
+       "return np.all((lo_a < hi_b) & (lo_b < hi_a), axis=-1)")]),
+    ("activeset.py", "a face's own vertices kept as candidates",
+     [("        hit[faces[f]] = False\n", "")]),
+    ("activeset.py", "margin added on one side only",
+     [("return pts.min(axis=1) - r, pts.max(axis=1) + r", "return pts.min(axis=1), pts.max(axis=1) + r")]),
+    ("activeset.py", "scene eps from the start positions only",
+     [("g = np.maximum(1.0, np.abs(np.concatenate([x0, x1])).max(axis=0))",
+       "g = np.maximum(1.0, np.abs(x0).max(axis=0))")]),
+    ("linesearch.py", "d_i as the largest distance",
+     [("d_i = min(d_i, float(linf_distance_batch(k, q, nthreads).min()))",
+       "d_i = min(d_i, float(linf_distance_batch(k, q, nthreads).max()))")]),
+    ("linesearch.py", "delta_i from the smallest tolerance",
+     [("delta_i = max(delta_i, float(tol.max()))", "delta_i = max(delta_i, float(tol.min()))")]),
+    ("linesearch.py", "alpha from the latest time of impact",
+     [("alpha = min(alpha, float(toi.min()))",
+       "alpha = min(alpha, float(np.where(np.isfinite(toi), toi, 0.0).max()))")]),
+    ("linesearch.py", "cap min and max swapped",
+     [('return min(x, delta) if cap == "min" else max(x, delta)',
+       'return max(x, delta) if cap == "min" else min(x, delta)')]),
+]
+PY_PINS = ["tests/test_oracle_linesearch.py", "tests/test_oracle_activeset.py"]
+
+
+def _py_tree(tmp, idx, module, subs):
+    """A scratch copy of what the Python-side pins import, with one module of
+    the oracle package mutated."""
+    d = os.path.join(tmp, f"py{idx}")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(d, "oracle"),
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    os.makedirs(os.path.join(d, "paper_2009_13349_gb300"))
+    for f in ("__init__.py", "workloads.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2009_13349_gb300", f),
+                    os.path.join(d, "paper_2009_13349_gb300", f))
+    os.makedirs(os.path.join(d, "tests"))
+    for f in ["tests/conftest.py", *PY_PINS]:
+        shutil.copy(os.path.join(ROOT, f), os.path.join(d, f))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
+    if module:
+        path = os.path.join(d, "oracle", module)
+        text = open(path).read()
+        for old, new in subs:
+            assert text.count(old) == 1, f"{module}: mutation site not unique: {old!r}"
+            text = text.replace(old, new)
+        open(path, "w").write(text)
+    return d
+
+
+def _run_py_pins(args):
+    d, lib = args
+    env = dict(os.environ, CCD_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
+    env.pop("PYTHONPATH", None)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu", *PY_PINS], cwd=d, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode
+
+
+def test_pins_kill_every_python_mutant():
+    with tempfile.TemporaryDirectory() as tmp:
+        lib = _build(tmp, "unmodified", [])
+        jobs = [(None, "unmodified", [])] + PY_MUTANTS
+        dirs = [_py_tree(tmp, i, m, subs) for i, (m, _, subs) in enumerate(jobs)]
+        workers = max(1, min(len(jobs), (os.cpu_count() or 2)))
+        with cf.ThreadPoolExecutor(workers) as ex:
+            codes = list(ex.map(_run_py_pins, [(d, lib) for d in dirs]))
+    assert codes[0] == 0, "the unmodified oracle copy must pass its pins"
+    survivors = [name for (_, name, _), c in zip(jobs[1:], codes[1:]) if c == 0]
+    assert not survivors, f"mutants not caught by any pin: {survivors}"
 
 
 def test_pins_kill_every_mutant():
