@@ -190,6 +190,12 @@ def cpu_baseline(wl, sample: int, seed: int = 123):
     return total_q / total_s, cores, total_s, total_q
 
 
+def workload_config(args):
+    """The simulation-mixed workload's config keys, the same for both arms."""
+    return {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
+            "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -207,8 +213,8 @@ def run_reference(args):
             k = max(1, int(round(args.ref_sample * b.n / wl.n)))
             idx = rng.choice(b.n, k, replace=False)
             t0 = time.perf_counter()
-            oracle.ccd_batch(b.kind, b.verts[idx], errs[b.kind], delta=1e-6, max_itr=10**6,
-                             nthreads=cores)
+            oracle.ccd_batch(b.kind, b.verts[idx], errs[b.kind], delta=1e-6,
+                             max_itr=args.max_itr, nthreads=cores)
             s += time.perf_counter() - t0
             q += k
         return q, s
@@ -227,9 +233,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ss / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"simulation-mixed {args.n} queries (VF:EE 1:1), seed {args.seed}",
-                   "delta": 1e-6, "max_itr": 10**6, "ms": 0.0,
-                   "sample_per_step": args.ref_sample},
+        "config": {**workload_config(args), "sample_per_step": args.ref_sample},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.ref_sample} random queries of the workload per step"},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
@@ -377,8 +381,7 @@ def run_native(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
-                   "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0,
+        "config": {**workload_config(args),
                    "l2": "inputs 192 MB per step > 129 MB L2; no flush",
                    "streams": "the VF and EE batches of a step on two CUDA streams",
                    "parallelism": f"{world} GPU(s), queries sharded, no collective"},
