@@ -141,6 +141,26 @@ def test_edge_cases(ccd, kind):
     assert np.all(g[3] == 1)
 
 
+def test_termination_branches(ccd):
+    """The inputs that pin the inside-C_eps termination (plain and under
+    minimum separation) and the depth guard in the oracle's tests: a tiny
+    static triangle with a point 2^-52 inside it, and a point resting on a
+    unit triangle with eps = 0 and delta = 1e-300."""
+    a, p = 2.0**-50, 2.0**-52
+    V = [0.0, 0.0, 0.0, a, 0.0, 0.0, 0.0, a, 0.0]
+    tiny = np.array([[p, p, 0.0, *V, p, p, 2.0**-51, *V]])
+    for ms in (0.0, 16 * 2.0**-52, 32 * 2.0**-52):
+        g, e = gpu_run(ccd, 0, tiny, ms=ms, delta=2.0**-52)
+        assert_parity(g, oracle_run(0, tiny, e, ms=ms, delta=2.0**-52), f"inside ms={ms}")
+    g, e = gpu_run(ccd, 0, tiny, delta=2.0**-52, err=np.full(3, 2.0**-52))
+    assert_parity(g, oracle_run(0, tiny, e, delta=2.0**-52), "not inside")
+    U1 = [0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0]
+    rest = np.array([[0.25, 0.25, 0.0, *U1, 0.25, 0.25, 0.0, *U1]])
+    g, e = gpu_run(ccd, 0, rest, delta=1e-300, err=np.zeros(3))
+    assert_parity(g, oracle_run(0, rest, e, delta=1e-300), "depth guard")
+    assert g[2][0] in (2.0**-53, 2.0**-52)
+
+
 def test_paper_examples(ccd, golden):
     for name in ("hourglass_vf.txt", "inflection_vf.txt", "bsc_false_negative_vf.txt"):
         q, meta = golden(name)

@@ -79,6 +79,17 @@ MUTANTS = [
        "double du = fabs(F[0][i][j][c] - F[1][i][j][c]);")]),
     ("per-query bound carried over from the previous query",
      [("        if (per_query) g[0] = g[1] = g[2] = 1.0;\n", "")]),
+    ("termination ignores B inside C_eps",
+     [("if (wB < delta || inside) {", "if (wB < delta) {")]),
+    ("inside test on the un-enlarged box",
+     [("if (!((m[c] - ms) >= -err[c] && (M[c] + ms) <= err[c])) inside = 0;",
+       "if (!(m[c] >= -err[c] && M[c] <= err[c])) inside = 0;")]),
+    ("inside test moves the box inward",
+     [("if (!((m[c] - ms) >= -err[c] && (M[c] + ms) <= err[c])) inside = 0;",
+       "if (!((m[c] + ms) >= -err[c] && (M[c] - ms) <= err[c])) inside = 0;")]),
+    ("reached tolerance from the enlarged box",
+     [("double w = M[c] - m[c];", "double w = (M[c] + ms) - (m[c] - ms);")]),
+    ("depth guard removed", [("if (R - L <= 0x1p-53) { /* depth guard */", "if (0) {")]),
     ("scene eps with the bound squared",
      [("            err_out[c] = K * ((g[c] * g[c]) * g[c]);",
        "            err_out[c] = K * (g[c] * g[c]);")]),

@@ -279,6 +279,71 @@ def test_minimum_separation_distance_semantics():
 
 
 # ---------------------------------------------------------------------------
+# Algorithm 2's second termination test, B inside C_eps (Sec. 4.2), and the
+# depth guard, on inputs where they alone decide
+# ---------------------------------------------------------------------------
+
+def _tiny_static_vf():
+    """A static triangle of legs 2^-50 and a point 2^-52 inside it that rises
+    by 2^-51 over the step.  Every corner of the root box is an exact dyadic,
+    so B_F([0,1]^3) is known in closed form: x and y span
+    [-3 * 2^-52, 2^-52], z spans [0, 2^-51]; w(B) = 2^-50."""
+    a, p = 2.0**-50, 2.0**-52
+    V = [0.0, 0.0, 0.0, a, 0.0, 0.0, 0.0, a, 0.0]
+    return np.array([p, p, 0.0, *V, p, p, 2.0**-51, *V])
+
+
+def test_inside_filter_box_terminates_at_first_check():
+    """With delta below w(B) the only way to stop at the root box is
+    B subset of C_eps: eps_VF = 30 * 2^-52 (gamma = 1) contains every axis
+    range above, so Algorithm 2 returns at check 1 with toi = 0 and the
+    reached tolerance w(B) = 2^-50 >= delta."""
+    qv = _tiny_static_vf()
+    e = oracle.err_from_bounds(0, qv)
+    assert np.all(e == 30 * 2.0**-52)
+    c, toi, tol, n = oracle.ccd(0, qv, e, delta=2.0**-52)
+    assert c and toi == 0.0 and n == 1 and tol == 2.0**-50
+    # the same box against eps = 2^-52: B is no longer inside, and w(B) >=
+    # delta, so the root box is split
+    c, toi, tol, n = oracle.ccd(0, qv, np.full(3, 2.0**-52), delta=2.0**-52)
+    assert c and n > 1
+
+
+def test_inside_test_uses_the_enlarged_box():
+    """Under minimum separation d the inside test takes the box enlarged by
+    d (Sec. 5.1): with eps = 34 * 2^-52 (Eq. msccd-error, gamma = 1) the
+    enlarged x range [-3 * 2^-52 - d, 2^-52 + d] lies in [-eps, eps] iff
+    d <= 31 * 2^-52.  So d = 16 * 2^-52 stops at check 1 and d = 32 * 2^-52
+    does not (its box still meets C_eps, and w(B) >= delta).  The reached
+    tolerance is the un-enlarged width 2^-50."""
+    qv = _tiny_static_vf()
+    e = oracle.err_from_bounds(0, qv, ms_nonzero=True)
+    assert np.all(e == 34 * 2.0**-52)
+    c, toi, tol, n = oracle.ccd(0, qv, e, ms=16 * 2.0**-52, delta=2.0**-52)
+    assert c and toi == 0.0 and n == 1 and tol == 2.0**-50
+    c, toi, tol, n = oracle.ccd(0, qv, e, ms=32 * 2.0**-52, delta=2.0**-52)
+    assert c and toi == 0.0 and n > 1
+
+
+def test_depth_guard_stops_at_width_2_to_the_minus_53():
+    """A static point exactly on a static triangle, eps = 0 and delta far
+    below any representable width: no box ever terminates, so only the
+    depth guard ends the run.  kappa_t = 0 (nothing moves), hence t is never
+    split and toi = 0; u and v alternate (kappa_u = kappa_v = 3) until the
+    split dimension has width 2^-53, after at most 2 * 53 levels of at most
+    eight boxes.  The box then returned has x and y ranges equal to its u
+    and v widths, 2^-53 or 2^-52, well above delta."""
+    V = [0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0]
+    p = [0.25, 0.25, 0.0]
+    qv = np.array([*p, *V, *p, *V])
+    np.testing.assert_array_equal(oracle.kappa(0, qv), [0.0, 3.0, 3.0])
+    c, toi, tol, n = oracle.ccd(0, qv, np.zeros(3), delta=1e-300, max_itr=10**6)
+    assert c and toi == 0.0
+    assert tol in (2.0**-53, 2.0**-52)
+    assert n <= 2 * 53 * 8
+
+
+# ---------------------------------------------------------------------------
 # The paper's worked examples (tests/golden)
 # ---------------------------------------------------------------------------
 
