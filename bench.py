@@ -1,14 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the batched FP64 inclusion-based CCD root finder on GB300.
 
-Workload (one "step"): the simulation-shaped mixed workload of 1,000,000
-queries (500,000 vertex-face + 500,000 edge-edge, seed 1): scene eps from
-bounds, then ccd_vf_batch and ccd_ee_batch, delta = 1e-6, m_I = 1e6, ms = 0.
-Inputs are resident in HBM when the timed region starts; they total 192 MB,
-more than the 129 MB L2, so no flush is needed between steps.
+Default workload (one "step"): 64 simulation instances with log-uniform
+query counts summing to 20,000,000 queries (VF:EE 1:1, seed 3, per-instance
+scale 10^U(-2,2) and eps, delta = 1e-6, m_I = 1e6, ms = 0), solved by one
+ccd_multi_batch call (per-segment eps from bounds, then the four solver
+stages) replayed from a CUDA graph, with launch shapes picked by the
+project's autotuner.  Inputs are resident in HBM when the timed region
+starts; they total 3.84 GB, far more than the 129 MB L2, so no flush is
+needed between steps.  The line also carries the plain form (one call per
+instance-kind), the 1,000,000-query simulation-shaped workload's rate, the
+roofline of the dominant kernel, an end-to-end rate through host buffers and
+the CPU oracle on a sample.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
-the host cores instead (bounded sample per step).
+the host cores instead (a bounded sample of the same workload per step).
+Other modes: ``--workload simulation-mixed | served | line-search |
+active-set``.
 """
 from __future__ import annotations
 
@@ -64,15 +72,15 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=500_000)
-    ap.add_argument("--ref-sample", type=int, default=50_000)
+    ap.add_argument("--cpu-sample", type=int, default=400_000)
+    ap.add_argument("--ref-sample", type=int, default=40_000)
     ap.add_argument("--max-itr", type=int, default=10**6,
                     help="check limit m_I of the simulation-mixed run (profiling cases only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deep-slots", type=int, default=None,
                     help="cap the deep-solver slots (smaller workspace, e.g. for profiling)")
-    ap.add_argument("--workload", default="simulation-mixed",
+    ap.add_argument("--workload", default="multi-instance",
                     choices=["simulation-mixed", "multi-instance", "served", "line-search",
                              "active-set"])
     ap.add_argument("--scale", type=float, default=1.0,
@@ -151,21 +159,59 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def recorded_traffic(batches):
-    """DRAM bytes per deep-solver launch (mean over the kinds in the step)
-    from the committed ncu record, or None if the kernel source changed since."""
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu record
+    (profiles/traffic.json, written by a capture of the current source), or
+    None if there is none or the kernel source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "deep_solver.traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2009_13349_gb300", "csrc", "ccd.cu")
     try:
-        rec = json.load(open(path))
+        rec = json.load(open(path)).get(kernel)
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except (OSError, ValueError):
+    except (OSError, ValueError, AttributeError):
         return None
-    if rec.get("sha256_prefix") != sha:
+    if not rec or rec.get("sha256_prefix") != sha:
         return None
-    per = [rec["dram_bytes_per_launch"]["VF" if b.kind == 0 else "EE"] for b in batches]
-    return float(sum(per) / len(per))
+    return rec
+
+
+STAGES = ["root_kernel", "pool_kernel (pooled small frontiers)",
+          "solve_kernel<32> (one-warp frontier)", "solve_kernel<256> (deep)"]
+
+
+def stage_ops(c: dict, stage: int, n_by_kind: dict) -> tuple[float, float]:
+    """(executed FP64 instructions, the same work evaluated check by check as
+    the definition reads) of one solver stage, from the kernels' own
+    counters; the *_ee counters split mixed-kind batches exactly."""
+    if stage == 0:
+        ops = sum(n * OPS_PER_CHECK[k] for k, n in n_by_kind.items())
+        return ops, ops
+    if stage == 1:
+        ee = c["evals_pool_ee"]
+        vf = c["evals_pool"] - ee
+        ops = vf * (2 * T_OPS[0] + BOX_OPS[0]) + ee * (2 * T_OPS[1] + BOX_OPS[1])
+        return ops, c["checks_pool"] * max(OPS_PER_CHECK.values())
+    if stage == 2:
+        tee, eee = c["tq_small_ee"], c["evals_small_ee"]
+        ops = ((c["tq_small"] - tee) * T_OPS[0] + tee * T_OPS[1]
+               + (c["evals_small"] - eee) * BOX_OPS[0] + eee * BOX_OPS[1])
+        return ops, c["checks_small"] * max(OPS_PER_CHECK.values())
+    tee, aee = c["tq_deep_ee"], c["a_tasks_deep_ee"]
+    shared = c["evals_shared_deep"]
+    ops = ((c["tq_deep"] - tee) * T_OPS[0] + tee * T_OPS[1] + (c["a_tasks_deep"] - aee) * A_OPS[0]
+           + aee * A_OPS[1] + shared * SHARED_BOX_OPS
+           + (c["evals_deep"] - shared) * max(BOX_OPS.values()))
+    return ops, c["checks_deep"] * max(OPS_PER_CHECK.values())
+
+
+def fp64_peak(ccd, sms):
+    """FP64 pipe rate measured in this run (fma.rn.f64 chains on every SM)."""
+    peak = 0.0
+    for _ in range(3):
+        ms, ops = ccd.fp64_peak_probe(sms * 8, 8192)
+        peak = max(peak, ops / (ms * 1e-3))
+    return peak
 
 
 def make_workload(n, seed):
@@ -173,50 +219,77 @@ def make_workload(n, seed):
     return W.simulation_mixed(n=n, seed=seed)
 
 
-def cpu_baseline(wl, sample: int, seed: int = 123):
-    """Oracle on a bounded random sample of the workload, all host cores."""
+def cpu_baseline(batches, sample: int, seed: int = 123, max_itr: int = 10**6):
+    """Oracle on a bounded random sample of the batches (sizes proportional),
+    each batch with its own scene eps, all host cores."""
     import oracle
     rng = np.random.default_rng(seed)
     cores = os.cpu_count() or 1
+    total = sum(b.n for b in batches)
+    picks = []
+    for b in batches:
+        k = min(b.n, max(1, int(round(sample * b.n / total))))
+        picks.append((b, np.sort(rng.choice(b.n, k, replace=False))))
     total_q, total_s = 0, 0.0
-    for b in wl.batches:
-        k = max(1, int(round(sample * b.n / wl.n)))
-        idx = rng.choice(b.n, k, replace=False)
-        err = oracle.err_from_bounds(b.kind, b.verts)      # scene eps of the full batch
+    for b, idx in picks:
+        err = oracle.err_from_bounds(b.kind, b.verts)      # eps of the whole instance
         t0 = time.perf_counter()
-        oracle.ccd_batch(b.kind, b.verts[idx], err, delta=1e-6, max_itr=10**6, nthreads=cores)
+        oracle.ccd_batch(b.kind, b.verts[idx], err, delta=1e-6, max_itr=max_itr, nthreads=cores)
         total_s += time.perf_counter() - t0
-        total_q += k
+        total_q += idx.size
     return total_q / total_s, cores, total_s, total_q
 
 
 def workload_config(args):
-    """The simulation-mixed workload's config keys, the same for both arms."""
+    """The simulation-mixed workload's config keys."""
     return {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
             "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0}
 
 
+def multi_config(n_total, scale):
+    """The multi-instance workload's config keys, the same for both arms."""
+    return {"workload": f"multi-instance: 64 simulation instances, {n_total} queries per GPU "
+                        f"(log-uniform 1k-2M each, VF:EE 1:1, per-instance scale 10^U(-2,2) "
+                        f"and eps), seed 3" + ("" if scale == 1.0 else f", scale {scale}"),
+            "delta": 1e-6, "max_itr": 10**6, "ms": 0.0}
+
+
+def multi_workload(scale, rank=0):
+    from paper_2009_13349_gb300 import parallel
+    from paper_2009_13349_gb300 import workloads as W
+    return W.multi_instance(count=64, total=int(20_000_000 * scale),
+                            seed=parallel.rank_seed(3, rank))
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores, every step a
+    bounded random sample of the multi-instance workload (each instance with
+    its own eps)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    wl = make_workload(args.n, args.seed)
+    wl = multi_workload(args.scale)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(7)
-    errs = {b.kind: oracle.err_from_bounds(b.kind, b.verts) for b in wl.batches}
+    errs = [oracle.err_from_bounds(b.kind, b.verts) for b in wl.batches]
+    sizes = np.array([b.n for b in wl.batches], dtype=np.float64)
 
     def step():
+        # args.ref_sample queries drawn over the whole workload, then solved
+        # instance by instance
+        owner = rng.choice(len(wl.batches), args.ref_sample, p=sizes / sizes.sum())
         q, s = 0, 0.0
-        for b in wl.batches:
-            k = max(1, int(round(args.ref_sample * b.n / wl.n)))
-            idx = rng.choice(b.n, k, replace=False)
+        for j in np.unique(owner):
+            b = wl.batches[j]
+            k = int(np.sum(owner == j))
+            idx = rng.choice(b.n, min(k, b.n), replace=False)
             t0 = time.perf_counter()
-            oracle.ccd_batch(b.kind, b.verts[idx], errs[b.kind], delta=1e-6,
-                             max_itr=args.max_itr, nthreads=cores)
+            oracle.ccd_batch(b.kind, b.verts[idx], errs[j], delta=1e-6, max_itr=10**6,
+                             nthreads=cores)
             s += time.perf_counter() - t0
-            q += k
+            q += idx.size
         return q, s
 
     for _ in range(args.warmup):
@@ -233,7 +306,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ss / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {**workload_config(args), "sample_per_step": args.ref_sample},
+        "config": {**multi_config(wl.n, args.scale), "sample_per_step": args.ref_sample},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.ref_sample} random queries of the workload per step"},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
@@ -243,21 +316,15 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def run_native(args):
+def measure_simulation_mixed(args, dev, steps, warmup, seed, stage_detail=True):
+    """The 1,000,000-query simulation-shaped workload: scene eps, then
+    ccd_vf_batch and ccd_ee_batch, each kind on its own stream.  Returns the
+    timing, stage and roofline figures and the buffers for the caller."""
     import torch
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     from paper_2009_13349_gb300 import ccd
-
-    from paper_2009_13349_gb300 import parallel
-    wl = make_workload(args.n, parallel.rank_seed(args.seed, rank))   # weak scaling
+    wl = make_workload(args.n, seed)
     batches = wl.batches
     verts = [ccd.to_soa(b.verts, dev) for b in batches]
-    host = [torch.from_numpy(np.ascontiguousarray(b.verts.T)).pin_memory() for b in batches]
     ws = [ccd.workspace(b.n, args.max_itr, dev, deep_slots=args.deep_slots) for b in batches]
     res = [ccd.Result(torch.empty(b.n, dtype=torch.uint8, device=dev),
                       torch.empty(b.n, dtype=torch.float64, device=dev),
@@ -281,14 +348,7 @@ def run_native(args):
         for sj in side:
             stream.wait_stream(sj)
 
-    # FP64 pipe peak, measured in this run (fma.rn.f64 chains, all SMs)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = 0.0
-    for _ in range(3):
-        ms, ops = ccd.fp64_peak_probe(sms * 8, 8192)
-        peak = max(peak, ops / (ms * 1e-3))
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
 
@@ -297,87 +357,90 @@ def run_native(args):
         e.record(stream)
         return e
 
-    stage_sets = [[[new_event() for _ in range(5)] for _ in batches] for _ in range(args.steps)]
-    marks = [new_event() for _ in range(args.steps + 1)]
+    stage_sets = [[[new_event() for _ in range(5)] for _ in batches] for _ in range(steps)]
+    marks = [new_event() for _ in range(steps + 1)]
     torch.cuda.synchronize(dev)
+    return {"wl": wl, "verts": verts, "ws": ws, "res": res, "side": side, "stream": stream,
+            "step": step, "stage_sets": stage_sets, "marks": marks}
+
+
+def simulation_mixed_figures(args, S, steps, peak):
+    """Stage times (per kind, and per stage the union of the kinds'
+    intervals), counters, truth checks and the roofline of a timed run."""
+    from paper_2009_13349_gb300 import ccd
+    batches, marks, stage_sets = S["wl"].batches, S["marks"], S["stage_sets"]
+    stage_ms = np.zeros((len(batches), 4))
+    span_ms = np.zeros(4)
+    for s in range(steps):
+        for k in range(4):
+            for j in range(len(batches)):
+                ev = stage_sets[s][j]
+                stage_ms[j, k] += ev[k].elapsed_time(ev[k + 1]) / steps
+            t0 = min(marks[s].elapsed_time(stage_sets[s][j][k]) for j in range(len(batches)))
+            t1 = max(marks[s].elapsed_time(stage_sets[s][j][k + 1]) for j in range(len(batches)))
+            span_ms[k] += (t1 - t0) / steps
+    counters = [ccd.workspace_counters(w) for w in S["ws"]]
+    fn, toi_bad, checks = 0, 0, []
+    for j, b in enumerate(batches):
+        col = S["res"][j].collides.cpu().numpy()
+        toi = S["res"][j].toi.cpu().numpy()
+        hit = b.truth == 1
+        fn += int(np.sum(col[hit] == 0))
+        toi_bad += int(np.sum(toi[hit] > b.t_star[hit]))
+        checks.append(S["res"][j].checks.cpu().numpy())
+    checks = np.concatenate(checks)
+    top = int(np.argmax(stage_ms.sum(axis=0)))
+    ops, naive = 0.0, 0.0
+    for j, b in enumerate(batches):
+        o, nv = stage_ops(counters[j], top, {b.kind: b.n})
+        ops += o
+        naive += nv
+    achieved = ops / (span_ms[top] * 1e-3)
+    return {"stage_ms": stage_ms, "span_ms": span_ms, "counters": counters, "fn": fn,
+            "toi_bad": toi_bad, "checks": checks, "top": top, "achieved": achieved,
+            "naive": naive / (span_ms[top] * 1e-3), "peak": peak}
+
+
+def run_native(args):
+    """--workload simulation-mixed: the 1,000,000-query simulation-shaped
+    workload on its own (its line of the earlier benchmark)."""
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2009_13349_gb300 import ccd, parallel
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp64_peak(ccd, sms)
+    S = measure_simulation_mixed(args, dev, args.steps, args.warmup,
+                                 parallel.rank_seed(args.seed, rank))
+    batches = S["wl"].batches
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = Clocks(local)
     clocks.start()
-    marks[0].record(stream)
+    S["marks"][0].record(S["stream"])
     for s in range(args.steps):
-        step(stage_sets[s])
-        marks[s + 1].record(stream)
+        S["step"](S["stage_sets"][s])
+        S["marks"][s + 1].record(S["stream"])
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
+    marks = S["marks"]
     step_ms = [marks[s].elapsed_time(marks[s + 1]) for s in range(args.steps)]
-    total_ms = marks[0].elapsed_time(marks[-1])
-    total_ms = parallel.max_over_ranks(total_ms, device=dev)
-    # stage times of each kind on its own stream (a stage may wait there for
-    # SMs the other kind's kernels hold), and per stage the union of the two
-    # kinds' intervals, which times the stage's work as a whole
-    stage_ms = np.zeros((len(batches), 4))
-    span_ms = np.zeros(4)
-    for s in range(args.steps):
-        for k in range(4):
-            for j in range(len(batches)):
-                ev = stage_sets[s][j]
-                stage_ms[j, k] += ev[k].elapsed_time(ev[k + 1]) / args.steps
-            t0 = min(marks[s].elapsed_time(stage_sets[s][j][k]) for j in range(len(batches)))
-            t1 = max(marks[s].elapsed_time(stage_sets[s][j][k + 1]) for j in range(len(batches)))
-            span_ms[k] += (t1 - t0) / args.steps
-    counters = [ccd.workspace_counters(w) for w in ws]
-
-    # correctness of the timed outputs against the constructed truths
-    fn, toi_bad, checks = 0, 0, []
-    for j, b in enumerate(batches):
-        col = res[j].collides.cpu().numpy()
-        toi = res[j].toi.cpu().numpy()
-        hit = b.truth == 1
-        fn += int(np.sum(col[hit] == 0))
-        toi_bad += int(np.sum(toi[hit] > b.t_star[hit]))
-        checks.append(res[j].checks.cpu().numpy())
-    checks = np.concatenate(checks)
-
-    # roofline of the dominant kernel
-    names = ["root_kernel", "pool_kernel (pooled small frontiers)",
-             "solve_kernel<32> (one-warp frontier)", "solve_kernel<256> (deep)"]
-    per_kernel = span_ms
-    top = int(np.argmax(stage_ms.sum(axis=0)))
-    # executed FP64 arithmetic, from the kernel's own counters
-    if top == 0:
-        alg_ops = sum(b.n * OPS_PER_CHECK[b.kind] for b in batches)
-        naive = alg_ops
-    elif top == 1:
-        alg_ops = sum(counters[j]["evals_pool"] * (2 * T_OPS[b.kind] + BOX_OPS[b.kind])
-                      for j, b in enumerate(batches))
-        naive = sum(counters[j]["checks_pool"] * OPS_PER_CHECK[b.kind]
-                    for j, b in enumerate(batches))
-    else:
-        sfx = "small" if top == 2 else "deep"
-        alg_ops = 0
-        for j, b in enumerate(batches):
-            c = counters[j]
-            shared = c["evals_shared_deep"] if sfx == "deep" else 0
-            per_box = BOX_OPS[b.kind]   # deep: every box goes through the shared partials
-            alg_ops += (c["tq_" + sfx] * T_OPS[b.kind] + (c["evals_" + sfx] - shared) * per_box
-                        + shared * SHARED_BOX_OPS)
-            if sfx == "deep":
-                alg_ops += c["a_tasks_deep"] * A_OPS[b.kind]
-        naive = sum(counters[j]["checks_" + sfx] * OPS_PER_CHECK[b.kind]
-                    for j, b in enumerate(batches))
-    achieved = alg_ops / (per_kernel[top] * 1e-3)
-    traffic = None
-    if names[top].startswith("solve_kernel<256>"):
-        traffic = recorded_traffic(batches)
+    total_ms = parallel.max_over_ranks(marks[0].elapsed_time(marks[-1]), device=dev)
+    F = simulation_mixed_figures(args, S, args.steps, peak)
+    top = F["top"]
+    rec = recorded_traffic("solve_kernel<256> simulation-mixed") if top == 3 else None
     total_queries = sum(b.n for b in batches) * world
-    value = parallel.job_throughput(sum(b.n for b in batches), world, total_ms / args.steps)
-
     out = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "metric": METRIC, "value": parallel.job_throughput(sum(b.n for b in batches), world,
+                                                           total_ms / args.steps),
+        "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -389,47 +452,43 @@ def run_native(args):
                    "parallelism": f"{world} GPU(s), queries sharded, no collective"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
-        "roofline": {"bound": "alu", "kernel": names[top], "achieved": achieved / 1e9,
-                     "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": achieved / peak,
-                     "traffic": traffic,
+        "roofline": {"bound": "alu", "kernel": STAGES[top], "achieved": F["achieved"] / 1e9,
+                     "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": F["achieved"] / peak,
+                     "traffic": rec["dram_bytes_per_launch"] if rec else None,
                      "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
                                     "(one FP64 pipe op = one add, mul or fma)",
                      "work": "executed FP64 add/sub/mul/fma instructions from the kernel's counters",
                      "duration": "per step, the union of the VF and EE launches' intervals "
                                  "(two streams)",
-                     "naive_equivalent_gops": naive / (per_kernel[top] * 1e-3) / 1e9},
-        "stage_ms_per_step": {("VF" if b.kind == 0 else "EE"): {names[k]: float(stage_ms[j, k])
+                     "naive_equivalent_gops": F["naive"] / 1e9},
+        "stage_ms_per_step": {("VF" if b.kind == 0 else "EE"): {STAGES[k]: float(F["stage_ms"][j, k])
                                                                for k in range(4)}
                               for j, b in enumerate(batches)},
-        "stage_union_ms_per_step": {names[k]: float(span_ms[k]) for k in range(4)},
-        "stage_note": "each kind on its own stream (a stage can wait for SMs the other kind "
-                      "holds); union: from the first start to the last end of the stage over "
-                      "both kinds",
-        "counters": {("VF" if b.kind == 0 else "EE"): counters[j] for j, b in enumerate(batches)},
-        "checks": {"mean": float(checks.mean()), "p50": float(np.percentile(checks, 50)),
-                   "p99": float(np.percentile(checks, 99)), "max": int(checks.max()),
-                   "early_termination_pct": float(100.0 * np.mean(checks >= args.max_itr))},
-        "false_negatives": fn, "toi_after_truth": toi_bad,
+        "stage_union_ms_per_step": {STAGES[k]: float(F["span_ms"][k]) for k in range(4)},
+        "counters": {("VF" if b.kind == 0 else "EE"): F["counters"][j]
+                     for j, b in enumerate(batches)},
+        "checks": {"mean": float(F["checks"].mean()),
+                   "p99": float(np.percentile(F["checks"], 99)), "max": int(F["checks"].max()),
+                   "early_termination_pct": float(100.0 * np.mean(F["checks"] >= args.max_itr))},
+        "false_negatives": F["fn"], "toi_after_truth": F["toi_bad"],
         "gpu_launches": args.steps * len(batches) * 8,
         "paper_context": PAPER_CONTEXT,
         "clocks": clk,
     }
-
     if not args.no_e2e:
-        h2d = sum(h.numel() * 8 for h in host)
-        d2h = sum(b.n * (1 + 8 + 8) for b in batches)
+        host = [torch.from_numpy(np.ascontiguousarray(b.verts.T)).pin_memory() for b in batches]
         out_host = [(torch.empty(b.n, dtype=torch.uint8).pin_memory(),
                      torch.empty(b.n, dtype=torch.float64).pin_memory(),
                      torch.empty(b.n, dtype=torch.float64).pin_memory()) for b in batches]
-        dres = [ccd.Result(r.collides, r.toi, r.out_tol, None) for r in res]
+        dres = [ccd.Result(r.collides, r.toi, r.out_tol, None) for r in S["res"]]
 
         def e2e_step():
             for j, b in enumerate(batches):
-                with torch.cuda.stream(side[j]):
-                    verts[j].copy_(host[j], non_blocking=True)
-                    err = ccd.err_from_bounds(b.kind, verts[j], stream=side[j])
-                    ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=args.max_itr, ws=ws[j],
-                              out=dres[j], stream=side[j])
+                with torch.cuda.stream(S["side"][j]):
+                    S["verts"][j].copy_(host[j], non_blocking=True)
+                    err = ccd.err_from_bounds(b.kind, S["verts"][j], stream=S["side"][j])
+                    ccd.batch(b.kind, S["verts"][j], err, delta=1e-6, max_itr=args.max_itr,
+                              ws=S["ws"][j], out=dres[j], stream=S["side"][j])
                     out_host[j][0].copy_(dres[j].collides, non_blocking=True)
                     out_host[j][1].copy_(dres[j].toi, non_blocking=True)
                     out_host[j][2].copy_(dres[j].out_tol, non_blocking=True)
@@ -441,13 +500,13 @@ def run_native(args):
             e2e_step()
         el = (time.perf_counter() - t0) / args.steps
         out["e2e"] = {"value": total_queries / el, "unit": "queries/s",
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "h2d_bytes_per_step": sum(h.numel() * 8 for h in host),
+                      "d2h_bytes_per_step": sum(b.n * (1 + 8 + 8) for b in batches),
                       "ms_per_step": el * 1e3}
-
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        qps, cores, secs, nq = cpu_baseline(wl, args.cpu_sample)
+        qps, cores, secs, nq = cpu_baseline(batches, args.cpu_sample, max_itr=args.max_itr)
         out["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores,
                                "kind": "oracle",
                                "sample": f"{nq} random queries of the workload ({secs:.1f} s)"}
@@ -461,16 +520,31 @@ def _gpu_name(torch, dev):
     return torch.cuda.get_device_properties(dev).name
 
 
+# our kernel launches per ccd_multi_batch call with its per-segment eps:
+# 3 (eps from bounds) + validation, level 0, pooled VF, pooled EE, one-warp,
+# order-by-level, deep
+MULTI_LAUNCHES = 10
+
+
 def run_multi_instance(args):
-    """64 simulation instances (log-uniform sizes, ~20M queries, VF:EE 1:1,
-    per-instance scale and eps): the plain form (one err + batch call per
-    instance-kind, in sequence) against the batched form (one multi-instance
-    call for all, replayed from a CUDA graph, autotuned launch shapes)."""
+    """The headline: 64 simulation instances (log-uniform sizes, 20M queries,
+    VF:EE 1:1, per-instance scale and eps) in one ccd_multi_batch call
+    replayed from a CUDA graph, autotuned launch shapes.  Extra keys: the
+    plain form (one call per instance-kind), the simulation-shaped 1M
+    workload, the roofline, e2e through host buffers, the oracle on a
+    sample."""
     import torch
-    from paper_2009_13349_gb300 import autotune, ccd
-    from paper_2009_13349_gb300 import workloads as W
-    dev = torch.device("cuda", 0)
-    wl = W.multi_instance(count=64, total=int(20_000_000 * args.scale), seed=3)
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2009_13349_gb300 import autotune, ccd, parallel
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp64_peak(ccd, sms)
+
+    wl = multi_workload(args.scale, rank)
     counts = [b.n for b in wl.batches]
     kinds = [b.kind for b in wl.batches]
     n = sum(counts)
@@ -495,49 +569,175 @@ def run_multi_instance(args):
     ccd.segments_err_from_bounds(sv, ssd)
 
     def measure(t):
-        ws = ccd.multi_workspace(acc, 10**6, t, dev)
+        wst = ccd.multi_workspace(acc, 10**6, t, dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        ccd.multi_batch(sv, ssd, 10**6, ws=ws, tuning=t, with_checks=False)
+        ccd.multi_batch(sv, ssd, 10**6, ws=wst, tuning=t, with_checks=False)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     tuning, timings = autotune.get_or_tune(_gpu_name(torch, dev), "multi-instance", measure,
                                            autotune.candidates(sms), reps=1, retune=args.retune)
     del sv, ssd
+    torch.cuda.empty_cache()
 
     out = ccd.Result(torch.empty(n, dtype=torch.uint8, device=dev),
                      torch.empty(n, dtype=torch.float64, device=dev),
-                     torch.empty(n, dtype=torch.float64, device=dev), None)
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.int64, device=dev))
     ws = ccd.multi_workspace(n, 10**6, tuning, dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for e in ev:
+        e.record(s)                       # creates the handles the library records into
     s.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(s):
         ccd.segments_err_from_bounds(verts, sd, stream=s)
         ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
     s.synchronize()
     g = torch.cuda.CUDAGraph()
+    ccd.set_stage_events(ev)              # recorded by the graph at every replay
     with torch.cuda.graph(g, stream=s):
         ccd.segments_err_from_bounds(verts, sd, stream=s)
         ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+    ccd.set_stage_events(None)
     for _ in range(args.warmup):
-        g.replay()
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    clocks = Clocks(0)
+        with torch.cuda.stream(s):
+            g.replay()
+    torch.cuda.synchronize(dev)
+
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stage_ms = np.zeros((args.steps, 4))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local)
     clocks.start()
-    ev[0].record(s)
+    graph_events = True
+    marks[0].record(s)
     for i in range(args.steps):
         with torch.cuda.stream(s):
             g.replay()
-        ev[i + 1].record(s)
-    torch.cuda.synchronize()
+        marks[i + 1].record(s)
+        s.synchronize()                   # the stage events are reused by every replay
+        if graph_events:
+            try:
+                stage_ms[i] = [ev[j].elapsed_time(ev[j + 1]) for j in range(4)]
+            except RuntimeError:
+                graph_events = False
+    torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    batched_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    if not graph_events:
+        # the graph's event nodes could not be timed: time the stages of the
+        # same call launched directly, right after the timed region
+        ccd.set_stage_events(ev)
+        for i in range(args.steps):
+            with torch.cuda.stream(s):
+                ccd.segments_err_from_bounds(verts, sd, stream=s)
+                ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+            s.synchronize()
+            stage_ms[i] = [ev[j].elapsed_time(ev[j + 1]) for j in range(4)]
+        ccd.set_stage_events(None)
+    if world > 1:
+        dist.barrier()
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
+    total_ms = parallel.max_over_ranks(marks[0].elapsed_time(marks[-1]), device=dev)
+    bm = total_ms / args.steps
+    counters = ccd.workspace_counters(ws, stream=s)
     batched = (out.collides.cpu().numpy(), out.toi.cpu().numpy(), out.out_tol.cpu().numpy())
+    checks = out.checks.cpu().numpy()
 
-    # plain form: one call per instance-kind, in sequence on one stream
+    # roofline of the dominant stage (all stages are one launch per call
+    # except the pooled stage, one per kind, back to back)
+    mean_stage = stage_ms.mean(axis=0)
+    top = int(np.argmax(mean_stage))
+    n_by_kind = {0: sum(c for c, k in zip(counts, kinds) if k == 0),
+                 1: sum(c for c, k in zip(counts, kinds) if k == 1)}
+    ops, naive = stage_ops(counters, top, n_by_kind)
+    achieved = ops / (mean_stage[top] * 1e-3)
+    kname = ("solve_kernel_seg<256> (deep)" if top == 3 else
+             STAGES[top].replace("solve_kernel<32>", "solve_kernel_seg<32>")
+             .replace("root_kernel", "root_kernel_seg"))
+    rec = recorded_traffic("solve_kernel_seg<256> multi-instance") if top == 3 else None
+
+    fn, toi_bad, off = 0, 0, 0
+    for b in wl.batches:
+        sl = slice(off, off + b.n)
+        hit = b.truth == 1
+        fn += int(np.sum(batched[0][sl][hit] == 0))
+        toi_bad += int(np.sum(batched[1][sl][hit] > b.t_star[hit]))
+        off += b.n
+
+    res = {
+        "metric": METRIC, "value": parallel.job_throughput(n, world, bm), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {**multi_config(n, args.scale),
+                   "form": "one ccd_multi_batch call (eps per segment + 4 solver stages) "
+                           "replayed from a CUDA graph",
+                   "tuning": tuning,
+                   "l2": f"inputs {192 * n / 1e9:.2f} GB per step > 129 MB L2; no flush",
+                   "parallelism": f"{world} GPU(s), each its own instance set, no collective"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": achieved / peak,
+                     "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                     "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
+                                    "(one FP64 pipe op = one add, mul or fma)",
+                     "work": "executed FP64 add/sub/mul/fma instructions from the kernel's "
+                             "counters (per kind)",
+                     "duration": ("mean CUDA-event time of the stage over the timed replays "
+                                  "(events recorded by the graph)" if graph_events else
+                                  "mean CUDA-event time of the stage over as many direct "
+                                  "launches of the same call right after the timed region"),
+                     "naive_equivalent_gops": naive / (mean_stage[top] * 1e-3) / 1e9},
+        "stage_ms_per_step": {STAGES[j]: float(mean_stage[j]) for j in range(4)},
+        "counters": counters,
+        "checks": {"mean": float(checks.mean()), "p99": float(np.percentile(checks, 99)),
+                   "max": int(checks.max()),
+                   "early_termination_pct": float(100.0 * np.mean(checks >= 10**6))},
+        "false_negatives": fn, "toi_after_truth": toi_bad,
+        "gpu_launches": args.steps * MULTI_LAUNCHES,
+        "paper_context": PAPER_CONTEXT,
+        "clocks": clk,
+        "autotune": None if timings is None else [[t, s_] for t, s_ in timings],
+    }
+
+    if not args.no_e2e:
+        # host buffers in, results out: the same graph between a pinned
+        # host -> device copy of the inputs and device -> host copies of the
+        # results, all on the call's stream
+        host = torch.empty((24, n), dtype=torch.float64).pin_memory()
+        host.copy_(verts.cpu())
+        out_host = (torch.empty(n, dtype=torch.uint8).pin_memory(),
+                    torch.empty(n, dtype=torch.float64).pin_memory(),
+                    torch.empty(n, dtype=torch.float64).pin_memory())
+
+        def e2e_step():
+            with torch.cuda.stream(s):
+                verts.copy_(host, non_blocking=True)
+                g.replay()
+                out_host[0].copy_(out.collides, non_blocking=True)
+                out_host[1].copy_(out.toi, non_blocking=True)
+                out_host[2].copy_(out.out_tol, non_blocking=True)
+            s.synchronize()
+
+        e2e_step()
+        k_e2e = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        el = (time.perf_counter() - t0) / k_e2e
+        assert np.array_equal(out_host[1].numpy(), batched[1])
+        res["e2e"] = {"value": n * world / el, "unit": "queries/s",
+                      "h2d_bytes_per_step": host.numel() * 8, "d2h_bytes_per_step": n * 17,
+                      "ms_per_step": el * 1e3, "steps": k_e2e,
+                      "api": "ccd_segments_err_from_bounds + ccd_multi_batch (graph)"}
+        del host, out_host
+
+    # the plain form: one eps + batch call per instance-kind, in sequence
     wsp = ccd.workspace(max(counts), 10**6, dev)
     plain_out = [None] * len(parts)
 
@@ -547,48 +747,63 @@ def run_multi_instance(args):
             plain_out[j] = ccd.batch(kind, t, e, delta=1e-6, max_itr=10**6, ws=wsp,
                                      out=plain_out[j], with_checks=False)
 
-    for _ in range(max(1, args.warmup)):
-        plain_step()
+    plain_step()
     torch.cuda.synchronize()
-    pev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    k_plain = 2
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(k_plain + 1)]
     pev[0].record()
-    for i in range(args.steps):
+    for i in range(k_plain):
         plain_step()
         pev[i + 1].record()
     torch.cuda.synchronize()
-    plain_ms = [pev[i].elapsed_time(pev[i + 1]) for i in range(args.steps)]
-    same = True
-    off = 0
+    plain_ms = [pev[i].elapsed_time(pev[i + 1]) for i in range(k_plain)]
+    same, off = True, 0
     for j, c in enumerate(counts):
         r = plain_out[j]
         same &= bool(np.array_equal(r.collides.cpu().numpy(), batched[0][off:off + c]))
         same &= bool(np.array_equal(r.toi.cpu().numpy(), batched[1][off:off + c]))
         same &= bool(np.array_equal(r.out_tol.cpu().numpy(), batched[2][off:off + c]))
         off += c
-    fn = 0
-    off = 0
-    for b in wl.batches:
-        hit = b.truth == 1
-        fn += int(np.sum(batched[0][off:off + b.n][hit] == 0))
-        off += b.n
-    bm, pm = float(np.mean(batched_ms)), float(np.mean(plain_ms))
-    print(json.dumps({
-        "metric": METRIC, "value": n / (bm * 1e-3), "unit": "queries/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"multi-instance: 64 instances, {n} queries (VF:EE 1:1), seed 3",
-                   "delta": 1e-6, "max_itr": 10**6, "form": "batched, CUDA graph replay",
-                   "tuning": tuning},
-        "plain": {"value": n / (pm * 1e-3), "ms_per_step": pm,
-                  "form": "one err + batch call per instance-kind (128 calls)"},
-        "speedup_vs_plain": pm / bm,
-        "latency_ms": {"p50": float(np.percentile(batched_ms, 50)),
-                       "p99": float(np.percentile(batched_ms, 99)),
-                       "plain_p50": float(np.percentile(plain_ms, 50)),
-                       "plain_p99": float(np.percentile(plain_ms, 99))},
-        "identical_to_plain": same, "false_negatives": fn, "clocks": clk,
-        "autotune": None if timings is None else [[t, s_] for t, s_ in timings],
-    }))
+    pm = float(np.mean(plain_ms))
+    res["plain"] = {"value": n / (pm * 1e-3), "ms_per_step": pm, "steps": k_plain,
+                    "form": f"one eps + batch call per instance-kind ({len(counts)} calls)",
+                    "identical_outputs": same}
+    res["speedup_vs_plain"] = pm / bm
+    del wsp, plain_out, parts
+    del ws, out
+    torch.cuda.empty_cache()
+
+    # the simulation-shaped 1M workload (the earlier headline), a few steps
+    k_sim = 5
+    S = measure_simulation_mixed(args, dev, k_sim, 2, parallel.rank_seed(args.seed, rank))
+    S["marks"][0].record(S["stream"])
+    for i in range(k_sim):
+        S["step"](S["stage_sets"][i])
+        S["marks"][i + 1].record(S["stream"])
+    torch.cuda.synchronize(dev)
+    F = simulation_mixed_figures(args, S, k_sim, peak)
+    sim_ms = S["marks"][0].elapsed_time(S["marks"][-1]) / k_sim
+    res["simulation_mixed_1m"] = {
+        "value": S["wl"].n / (sim_ms * 1e-3), "ms_per_step": sim_ms, "steps": k_sim,
+        "workload": workload_config(args)["workload"],
+        "dominant_kernel": STAGES[F["top"]], "dominant_frac_of_peak": F["achieved"] / peak,
+        "dominant_ms": float(F["span_ms"][F["top"]]),
+        "false_negatives": F["fn"], "toi_after_truth": F["toi_bad"]}
+    del S
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        qps, cores, secs, nq = cpu_baseline(wl.batches, args.cpu_sample)
+        res["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{nq} random queries of the workload, spread over the "
+                                         f"instances by size ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_served(args):

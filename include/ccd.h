@@ -130,7 +130,8 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
                                 int32_t *fallbacks, void *stream);
 
 /*
- * Counters of the last batch that used `workspace` (synchronizes `stream`):
+ * Counters of the last batch that used `workspace` (synchronizes `stream`);
+ * the first min(count, CCD_NUM_COUNTERS) are written to `counters`:
  * [0] queries that survived the level-0 check, [1] queries moved to the deep
  * solver, [2] capacity fallbacks, [3] sum of check counts n of queries
  * finished by the small-frontier solver, [4] the same for the deep solver,
@@ -145,10 +146,14 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * them), [13] queries the pooled solver handed to
  * the one-warp solver, [14] sum of check counts n of queries finished by
  * the pooled solver, [15] box evaluations executed by the pooled solver
- * (each computes its own t-quantities at t_L and t_R).  The small-frontier
- * solver of [3], [5], [8] is the one-warp solver.
+ * (each computes its own t-quantities at t_L and t_R), [16] and [17] the
+ * edge-edge parts of [9] and [10], [18] of [15], [19] of [8] and [20] of [5]
+ * (the vertex-face part is the difference).  The small-frontier solver of
+ * [3], [5], [8] is the one-warp solver.
  */
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[16], void *stream);
+#define CCD_NUM_COUNTERS 21
+ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int32_t count,
+                                  void *stream);
 
 /*
  * Optional stage timing for benchmarks: with count == 5, every following

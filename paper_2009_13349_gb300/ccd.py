@@ -51,7 +51,8 @@ def lib():
         L.ccd_workspace_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32), vp]
         L.ccd_workspace_status.restype = ctypes.c_int
-        L.ccd_workspace_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.ccd_workspace_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                             vp]
         L.ccd_workspace_counters.restype = ctypes.c_int
         L.ccd_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
         L.ccd_set_stage_events.restype = ctypes.c_int
@@ -213,12 +214,14 @@ def workspace_status(ws: torch.Tensor, stream=None):
 COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "checks_deep",
                  "evals_small", "evals_deep", "status", "tq_small", "tq_deep", "a_tasks_deep",
                  "split_chunks_deep", "evals_shared_deep", "mid_queries", "checks_pool",
-                 "evals_pool")
+                 "evals_pool", "tq_deep_ee", "a_tasks_deep_ee", "evals_pool_ee", "tq_small_ee",
+                 "evals_small_ee")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
     arr = (ctypes.c_int64 * len(COUNTER_NAMES))()
-    _check(lib().ccd_workspace_counters(_ptr(ws), arr, _stream(stream)), "ccd_workspace_counters")
+    _check(lib().ccd_workspace_counters(_ptr(ws), arr, len(COUNTER_NAMES), _stream(stream)),
+           "ccd_workspace_counters")
     return dict(zip(COUNTER_NAMES, list(arr)))
 
 

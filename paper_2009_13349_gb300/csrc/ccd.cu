@@ -96,7 +96,13 @@ struct Header {
     unsigned long long checks_pool;   // sum of n over queries finished by the pooled solver
     unsigned long long evals_pool;    // box evaluations executed by the pooled solver
     int head_pool_ee;                 // work counter of the EE pooled solver (segmented batches)
-    int pad[33];
+    int pad0;
+    unsigned long long tq_deep_ee;      // the part of tq_deep spent on edge-edge queries
+    unsigned long long a_tasks_deep_ee; // the part of a_tasks_deep spent on edge-edge queries
+    unsigned long long evals_pool_ee;   // the part of evals_pool spent on edge-edge queries
+    unsigned long long tq_small_ee;     // the part of tq_small spent on edge-edge queries
+    unsigned long long evals_small_ee;  // the part of evals_small spent on edge-edge queries
+    int pad[22];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -684,6 +690,7 @@ __global__ void __launch_bounds__(ROOT_THREADS) root_kernel(Params p)
 // Bound used to size the deep slots: every box of level l+1 is a child of a
 // colliding box of level l whose check index n was below m_I (otherwise the
 // query returned), so a level never holds more than 2 (m_I - 1) boxes.
+template <int KIND>
 __device__ __forceinline__ void count_done(const Params &p, bool deep, long long n,
                                            unsigned long long evals, unsigned long long tqs,
                                            unsigned long long atasks = 0,
@@ -693,8 +700,13 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
     atomicAdd(deep ? &p.hdr->checks_deep : &p.hdr->checks_small, (unsigned long long)n);
     atomicAdd(deep ? &p.hdr->evals_deep : &p.hdr->evals_small, evals);
     atomicAdd(deep ? &p.hdr->tq_deep : &p.hdr->tq_small, tqs);
+    if (KIND == CCD_KIND_EE) {
+        atomicAdd(deep ? &p.hdr->tq_deep_ee : &p.hdr->tq_small_ee, tqs);
+        if (!deep) atomicAdd(&p.hdr->evals_small_ee, evals);
+    }
     if (atasks | split_chunks | shared_evals) {
         atomicAdd(&p.hdr->a_tasks_deep, atasks);
+        if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->a_tasks_deep_ee, atasks);
         atomicAdd(&p.hdr->split_chunks_deep, split_chunks);
         atomicAdd(&p.hdr->evals_shared_deep, shared_evals);
     }
@@ -990,7 +1002,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                         if (tid == 0) {
                             write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w,
                                          nfc);
-                            count_done(p, fallback, nfc, evals, tqs, atasks, split_chunks,
+                            count_done<KIND>(p, fallback, nfc, evals, tqs, atasks, split_chunks,
                                        shared_evals);
                         }
                         return true;
@@ -1001,7 +1013,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     if (tid == 0) {
                         write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])),
                                      s.dec[wc].w_cut, ncut);
-                        count_done(p, fallback, ncut, evals, tqs, atasks, split_chunks, shared_evals);
+                        count_done<KIND>(p, fallback, ncut, evals, tqs, atasks, split_chunks, shared_evals);
                     }
                     return true;
                 }
@@ -1015,7 +1027,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
-                count_done(p, fallback, n_before + size, evals, tqs, atasks, split_chunks, shared_evals);
+                count_done<KIND>(p, fallback, n_before + size, evals, tqs, atasks, split_chunks, shared_evals);
             }
             return true;
         }
@@ -1099,7 +1111,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
         }
         if (nchild > cap) {
             if (!fallback) {
-                if (tid == 0) count_done(p, false, 0, evals, tqs);
+                if (tid == 0) count_done<KIND>(p, false, 0, evals, tqs);
                 hand_level = k[0] + k[1] + k[2];
                 return false;
             }
@@ -1108,7 +1120,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w, n_before);
                 atomicExch(&p.hdr->status, (int)CCD_ERR_CAPACITY);
                 atomicAdd(&p.hdr->fallbacks, 1);
-                count_done(p, true, n_before, evals, tqs, atasks, split_chunks, shared_evals);
+                count_done<KIND>(p, true, n_before, evals, tqs, atasks, split_chunks, shared_evals);
             }
             return true;
         }
@@ -1513,6 +1525,7 @@ __global__ void __launch_bounds__(32)
         __syncwarp();
     }
     atomicAdd(&p.hdr->evals_pool, evals);
+    if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->evals_pool_ee, evals);
     atomicAdd(&p.hdr->checks_pool, checks_done);
 }
 
@@ -2006,9 +2019,17 @@ bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout
 cudaEvent_t g_stage_events[5];
 int g_stage_events_on = 0;
 
+// Inside a stream capture a plain event record only orders the captured
+// work; the external flag makes it a node of the graph, so that every replay
+// records the event (and the stages of a replayed batch can be timed).
 inline void stage_mark(int i, cudaStream_t st)
 {
-    if (g_stage_events_on) cudaEventRecord(g_stage_events[i], st);
+    if (!g_stage_events_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(g_stage_events[i], st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(g_stage_events[i], st);
 }
 
 template <int KIND>
@@ -2156,30 +2177,23 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status, int32_t 
     return CCD_OK;
 }
 
-ccd_status ccd_workspace_counters(const void *workspace, int64_t counters[16], void *stream)
+ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int32_t count,
+                                  void *stream)
 {
-    if (!workspace || !counters) return CCD_ERR_ARG;
+    if (!workspace || !counters || count < 0) return CCD_ERR_ARG;
     Header h;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(&h, workspace, sizeof(Header), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return CCD_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCD_ERR_CUDA;
-    counters[0] = h.survivors;
-    counters[1] = h.overflow;
-    counters[2] = h.fallbacks;
-    counters[3] = (int64_t)h.checks_small;
-    counters[4] = (int64_t)h.checks_deep;
-    counters[5] = (int64_t)h.evals_small;
-    counters[6] = (int64_t)h.evals_deep;
-    counters[7] = h.status;
-    counters[8] = (int64_t)h.tq_small;
-    counters[9] = (int64_t)h.tq_deep;
-    counters[10] = (int64_t)h.a_tasks_deep;
-    counters[11] = (int64_t)h.split_chunks_deep;
-    counters[12] = (int64_t)h.evals_shared_deep;
-    counters[13] = h.mid;
-    counters[14] = (int64_t)h.checks_pool;
-    counters[15] = (int64_t)h.evals_pool;
+    const int64_t all[CCD_NUM_COUNTERS] = {
+        h.survivors, h.overflow, h.fallbacks, (int64_t)h.checks_small, (int64_t)h.checks_deep,
+        (int64_t)h.evals_small, (int64_t)h.evals_deep, h.status, (int64_t)h.tq_small,
+        (int64_t)h.tq_deep, (int64_t)h.a_tasks_deep, (int64_t)h.split_chunks_deep,
+        (int64_t)h.evals_shared_deep, h.mid, (int64_t)h.checks_pool, (int64_t)h.evals_pool,
+        (int64_t)h.tq_deep_ee, (int64_t)h.a_tasks_deep_ee, (int64_t)h.evals_pool_ee,
+        (int64_t)h.tq_small_ee, (int64_t)h.evals_small_ee};
+    for (int i = 0; i < count && i < CCD_NUM_COUNTERS; ++i) counters[i] = all[i];
     return CCD_OK;
 }
 

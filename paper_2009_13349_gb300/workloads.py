@@ -356,8 +356,94 @@ def simulation_mixed(n: int = 1_000_000, seed: int = 1, frac_collide: float = 0.
 # Degenerate-heavy workload on a 2^-20 grid
 # ---------------------------------------------------------------------------
 
+def _cross2(a, b):
+    return a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0]
+
+
+def _place(L, ax):
+    """Local (a, b, normal) coordinates -> global axes, the normal along ``ax``
+    (a permutation of coordinates: exact)."""
+    G = np.empty_like(L)
+    idx = np.arange(L.shape[0])
+    for k, off in enumerate((1, 2, 0)):
+        G[idx, ..., (ax + off) % 3] = L[..., k]
+    return G
+
+
+def _grazing(rng, m, kind):
+    """Tangent contact: the primitives touch at one time t* only, with zero
+    normal speed there.  In local coordinates (a, b, normal) the second
+    primitive (VF triangle / EE edge p3 p4) lies at t* in the plane n = c and
+    its points rise at rates w = L(x) for an affine L(x) = l0 + g . x over the
+    plane, while the whole scene drifts by m in (a, b).  The first primitive's
+    points are placed in that plane at t* (VF: the point at barycentric
+    (u*, v*) of the triangle; EE: an edge crossing p3 p4 at (u*, v*)), drift
+    by m + s, and rise at L of their own position at t*.  The plane's height
+    under such a point is then c + (t - t*) L(x) + (t - t*)^2 g . s, so its
+    normal offset is -(t - t*)^2 g . s: zero only at t*, with zero speed.
+    Grids: positions 2^-8, (u*, v*) 2^-4, l0 and g 2^-2, t* 2^-6, drifts
+    2^-14, so every coordinate lies on the 2^-20 grid and the contact is
+    exact in binary64.  Returns (queries, t*)."""
+    t = rng.integers(1, 64, m) / 64.0
+    c = q(rng.uniform(-1, 1, m), 2.0**-8)
+    l0 = q(rng.uniform(-1, 1, m), 2.0**-2)
+    g = q(rng.uniform(-1, 1, (m, 2)), 2.0**-2)
+    drift = q(rng.normal(0, 0.3, (m, 2)), 2.0**-14)
+    s = q(rng.normal(0, 0.3, (m, 2)), 2.0**-14)
+    # keep g . s away from 0: the contact must be a single tangent touch
+    bad = np.abs(np.sum(g * s, -1)) < 0.02
+    while bad.any():
+        g[bad] = q(rng.uniform(-1, 1, (bad.sum(), 2)), 2.0**-2)
+        s[bad] = q(rng.normal(0, 0.3, (bad.sum(), 2)), 2.0**-14)
+        bad = np.abs(np.sum(g * s, -1)) < 0.02
+    Lf = lambda x: l0[:, None] + np.sum(g[:, None, :] * x, -1)   # x: (m, k, 2)
+    if kind == VF:
+        tri = q(rng.uniform(-1, 1, (m, 3, 2)), 2.0**-8)
+        area = np.abs(_cross2(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]))
+        while (area < 0.1).any():
+            k = area < 0.1
+            tri[k] = q(rng.uniform(-1, 1, (k.sum(), 3, 2)), 2.0**-8)
+            area = np.abs(_cross2(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]))
+        # (u*, v*) on the 2^-4 grid, u*, v* >= 1/16, u* + v* <= 15/16
+        u = rng.integers(1, 15, m)
+        v = rng.integers(1, 15, m)
+        over = u + v > 15
+        u[over], v[over] = 15 - u[over], 15 - v[over]
+        u, v = u / 16.0, v / 16.0
+        pt = (1 - u - v)[:, None] * tri[:, 0] + u[:, None] * tri[:, 1] + v[:, None] * tri[:, 2]
+        X = np.concatenate([pt[:, None], tri], 1)              # (m, 4, 2) at t*
+        vel = np.concatenate([(drift + s)[:, None], np.repeat(drift[:, None], 3, 1)], 1)
+    else:
+        B = q(rng.uniform(-1, 1, (m, 2, 2)), 2.0**-8)
+        E = q(rng.uniform(-1, 1, (m, 2)), 2.0**-8)
+        cr = np.abs(_cross2(E, B[:, 1] - B[:, 0]))
+        while (cr < 0.1).any():
+            k = cr < 0.1
+            B[k] = q(rng.uniform(-1, 1, (k.sum(), 2, 2)), 2.0**-8)
+            E[k] = q(rng.uniform(-1, 1, (k.sum(), 2)), 2.0**-8)
+            cr = np.abs(_cross2(E, B[:, 1] - B[:, 0]))
+        u = rng.integers(1, 16, m) / 16.0
+        v = rng.integers(1, 16, m) / 16.0
+        Xc = (1 - v)[:, None] * B[:, 0] + v[:, None] * B[:, 1]
+        A = np.stack([Xc - u[:, None] * E, Xc + (1 - u)[:, None] * E], 1)
+        X = np.concatenate([A, B], 1)
+        vel = np.concatenate([np.repeat((drift + s)[:, None], 2, 1),
+                              np.repeat(drift[:, None], 2, 1)], 1)
+    w = Lf(X)                                                  # (m, 4) rise rates
+    L0 = np.concatenate([X - t[:, None, None] * vel,
+                         (c[:, None] - t[:, None] * w)[..., None]], -1)
+    L1 = np.concatenate([X + (1 - t)[:, None, None] * vel,
+                         (c[:, None] + (1 - t)[:, None] * w)[..., None]], -1)
+    ax = rng.integers(0, 3, m)
+    return _pack(_place(L0, ax), _place(L1, ax)), t
+
+
 def _degenerate_family(rng, m, kind, fam):
+    """One degenerate family on the 2^-20 grid.  Returns (queries, t*): t* is
+    an exact contact time for the constructed families (vertex-on-vertex and
+    grazing), NaN otherwise."""
     gg = 2.0**-20
+    tstar = np.full(m, np.nan)
     P0 = q(rng.uniform(-1, 1, (m, 4, 3)), gg)
     P1 = q(P0 + rng.normal(0, 0.3, (m, 4, 3)), gg)
     idx = np.arange(m)
@@ -367,17 +453,16 @@ def _degenerate_family(rng, m, kind, fam):
         P0[idx, :, ax] = c[:, None]
         P1[idx, :, ax] = c[:, None]
     elif fam == FAM_COLLINEAR:
-        # all points on one moving line: x(s) = a + s d with grid s
+        # all points on one moving line: x(s) = a + s d, s on 2^-8, d on 2^-12
         a0 = q(rng.uniform(-1, 1, (m, 3)), gg)
-        d0 = q(rng.uniform(-1, 1, (m, 3)), gg)
+        d0 = q(rng.uniform(-1, 1, (m, 3)), 2.0**-12)
         a1 = q(a0 + rng.normal(0, 0.3, (m, 3)), gg)
-        d1 = d0
         s = q(rng.uniform(-1, 1, (m, 4)), 2.0**-8)
         P0 = a0[:, None] + s[..., None] * d0[:, None]
         s1 = q(s + rng.normal(0, 0.3, (m, 4)), 2.0**-8)
-        P1 = a1[:, None] + s1[..., None] * d1[:, None]
+        P1 = a1[:, None] + s1[..., None] * d0[:, None]
     elif fam == FAM_PARALLEL:
-        d = q(rng.uniform(-1, 1, (m, 3)), gg)
+        d = q(rng.uniform(-1, 1, (m, 3)), 2.0**-16)
         off = q(rng.normal(0, 0.05, (m, 3)), gg)
         sc = q(rng.uniform(0.25, 1.5, m), 2.0**-4)[:, None]
         a0 = P0[:, 0]
@@ -389,44 +474,40 @@ def _degenerate_family(rng, m, kind, fam):
             P0[:, 3] = q(P0[:, 1] + rng.uniform(-1, 1, (m, 3)), gg)
             P1[:, 3] = P0[:, 3]
     elif fam == FAM_VERTEX:
-        # a vertex of the first primitive meets a vertex of the second at t*
-        t = q(rng.uniform(0, 1, m), 2.0**-10)
-        Vt = _interp(P0[:, 2], P1[:, 2], t) if kind == EE else _interp(P0[:, 1], P1[:, 1], t)
-        Dp = P1[:, 0] - P0[:, 0]
-        P0[:, 0] = Vt - t[:, None] * Dp
-        P1[:, 0] = Vt + (1 - t)[:, None] * Dp
-    elif fam == FAM_GRAZING:
-        # coplanar motion whose path passes exactly through a vertex (tangent
-        # contact of zero normal speed): plane fixed, point grazes vertex v1/p3
-        ax = rng.integers(0, 3, m)
-        c = q(rng.uniform(-1, 1, m), gg)
-        P0[idx, :, ax] = c[:, None]
-        P1[idx, :, ax] = c[:, None]
-        t = q(rng.uniform(0, 1, m), 2.0**-10)
+        # a vertex of the first primitive meets a vertex of the second (VF: p
+        # meets v1; EE: p1 meets p3) at t* on a 2^-4 grid; positions on 2^-16
+        P0 = q(P0, 2.0**-16)
+        P1 = q(P1, 2.0**-16)
+        t = rng.integers(1, 16, m) / 16.0
         j = 1 if kind == VF else 2
         Vt = _interp(P0[:, j], P1[:, j], t)
         Dp = P1[:, 0] - P0[:, 0]
         P0[:, 0] = Vt - t[:, None] * Dp
         P1[:, 0] = Vt + (1 - t)[:, None] * Dp
-    return _pack(P0, P1)
+        tstar = t
+    elif fam == FAM_GRAZING:
+        return _grazing(rng, m, kind)
+    return _pack(P0, P1), tstar
 
 
 def degenerate_heavy(n: int = 100_000, seed: int = 2) -> Workload:
     """Degenerate-heavy workload on a 2^-20 grid (VF:EE 1:1): coplanar,
     collinear, parallel-edge, vertex-on-vertex and grazing-tangent motions in
-    equal parts."""
+    equal parts.  Vertex-on-vertex and grazing queries are constructed
+    contacts (truth 1, exact t*); the others are unlabelled."""
     rng = np.random.default_rng(seed)
     fams = [FAM_COPLANAR, FAM_COLLINEAR, FAM_PARALLEL, FAM_VERTEX, FAM_GRAZING]
     batches = []
     for kind, nk in ((VF, n - n // 2), (EE, n // 2)):
         fam = np.array([fams[i % len(fams)] for i in range(nk)], np.int8)
         verts = np.empty((nk, 24))
+        tstar = np.full(nk, np.nan)
         for f in fams:
             idx = np.nonzero(fam == f)[0]
-            verts[idx] = _degenerate_family(rng, idx.size, kind, f)
+            verts[idx], tstar[idx] = _degenerate_family(rng, idx.size, kind, f)
+        truth = np.where(np.isnan(tstar), -1, 1).astype(np.int8)
         perm = rng.permutation(nk)
-        batches.append(Batch(kind, verts[perm], np.full(nk, -1, np.int8),
-                             np.full(nk, np.nan), fam[perm]))
+        batches.append(Batch(kind, verts[perm], truth[perm], tstar[perm], fam[perm]))
     return Workload("degenerate-heavy", batches,
                     {"seed": seed, "n": n, "ms": (0.0, 1e-4), "delta": 1e-6,
                      "max_itr": 10**6})

@@ -1,0 +1,140 @@
+"""GPU parity at the stated sizes of the degenerate-heavy and multi-instance
+workloads, against the CPU oracle.
+
+Degenerate-heavy: 100,000 queries (VF:EE 1:1, seed 2, coordinates on a
+2^-20 grid; coplanar, collinear, parallel-edge, vertex-on-vertex and
+grazing-tangent motions), run twice, with ms = 0 and ms = 1e-4 (Sec. 5.1),
+delta = 1e-6, m_I = 1e6.  Every one of the 200,000 GPU answers of a
+constructed contact (vertex-on-vertex and grazing: 40 % of the queries) must
+collide with toi <= t*.  The oracle checks a random sample of each kind and
+ms; it is slow on this workload (about 0.85 us per check per core, and a
+quarter to two thirds of the queries run to the 10^6-check limit), so the
+sample is 5,000 queries per kind at ms = 0 and 2,000 per kind at ms = 1e-4.
+
+Multi-instance: 64 simulation instances with log-uniform sizes summing to
+20,000,000 queries (seed 3), per-instance scale and eps, in one segmented
+call captured in a CUDA graph and replayed; a random sample of every
+instance-kind segment against the oracle, every constructed collision
+against its truth.
+
+The bar is the one of the other parity tests: flags bit-exact, toi and
+out_tol equal (the stated |dtoi| <= 1e-6 is also asserted), check counts
+equal.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_13349_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 1
+TOI_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ccd():
+    from paper_2009_13349_gb300 import ccd as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _host(r):
+    return (r.collides.cpu().numpy(), r.toi.cpu().numpy(), r.out_tol.cpu().numpy(),
+            r.checks.cpu().numpy())
+
+
+def _assert_parity(g, o, label):
+    gc, gt, gw, gk = g
+    oc, ot, ow, ok = o
+    bad = np.nonzero(gc != oc)[0]
+    assert bad.size == 0, f"{label}: {bad.size} flag mismatches, e.g. {bad[:8]}"
+    hit = oc == 1
+    assert np.all(np.abs(gt[hit] - ot[hit]) <= TOI_TOL), f"{label}: toi beyond 1e-6"
+    for name, x, y in (("toi", gt, ot), ("out_tol", gw, ow), ("checks", gk, ok)):
+        bad = np.nonzero(x != y)[0]
+        assert bad.size == 0, f"{label}: {bad.size} {name} differ, e.g. {bad[:8]}"
+
+
+def _assert_truth(col, toi, truth, t_star, label):
+    hit = truth == 1
+    assert np.all(col[hit] == 1), f"{label}: {np.sum(col[hit] == 0)} false negatives"
+    assert np.all(toi[hit] <= t_star[hit]), f"{label}: toi after a constructed contact"
+    assert np.all(col[truth == 0] == 0), f"{label}: a certified separation reported"
+
+
+@pytest.mark.parametrize("ms,sample", [(0.0, 5000), (1e-4, 2000)])
+def test_degenerate_heavy_100k(ccd, ms, sample):
+    wl = W.degenerate_heavy(n=100_000, seed=2)
+    rng = np.random.default_rng(202 + int(ms > 0))
+    for b in wl.batches:
+        err = oracle.err_from_bounds(b.kind, b.verts, ms_nonzero=ms > 0)
+        v = ccd.to_soa(b.verts)
+        e_gpu = ccd.err_from_bounds(b.kind, v, ms_nonzero=ms > 0)
+        assert np.array_equal(e_gpu.cpu().numpy(), err)
+        g = _host(ccd.batch(b.kind, v, e_gpu, ms=ms, delta=1e-6, max_itr=10**6))
+        label = f"degenerate-heavy kind={b.kind} ms={ms}"
+        _assert_truth(g[0], g[1], b.truth, b.t_star, label)
+        idx = np.sort(rng.choice(b.n, sample, replace=False))
+        o = oracle.ccd_batch(b.kind, b.verts[idx], err, ms=ms, delta=1e-6, max_itr=10**6,
+                             nthreads=NT)
+        _assert_parity(tuple(x[idx] for x in g), o, label)
+        # the sample spans the deep end of the workload
+        assert np.mean(o[3] >= 10**5) > 0.1
+
+
+def test_multi_instance_20m_graph_replay(ccd):
+    wl = W.multi_instance(count=64, total=20_000_000, seed=3)
+    counts = [b.n for b in wl.batches]
+    kinds = [b.kind for b in wl.batches]
+    n = sum(counts)
+    dev = torch.device("cuda")
+    verts = torch.empty((24, n), dtype=torch.float64, device=dev)
+    off = 0
+    for b in wl.batches:
+        verts[:, off:off + b.n].copy_(ccd.to_soa(b.verts, dev))
+        off += b.n
+    seg = ccd.make_segments(counts, kinds, 0.0, 1e-6, 10**6)
+    sd = ccd.segments_to_device(seg, dev)
+    ws = ccd.multi_workspace(n, 10**6, None, dev)
+    out = ccd.Result(torch.empty(n, dtype=torch.uint8, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.int64, device=dev))
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):                                  # warm-up outside capture
+        ccd.segments_err_from_bounds(verts, sd, stream=s)
+        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ccd.segments_err_from_bounds(verts, sd, stream=s)
+        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, stream=s)
+    out.collides.zero_()
+    out.checks.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    first = _host(out)
+    g.replay()
+    torch.cuda.synchronize()
+    got = _host(out)
+    for a, b in zip(first, got):
+        assert np.array_equal(a, b), "replays differ"
+    assert ccd.workspace_status(ws)[0] == 0
+    segs = ccd.segments_from_device(sd)
+    rng = np.random.default_rng(303)
+    off = 0
+    for s_i, b in enumerate(wl.batches):
+        sl = slice(off, off + b.n)
+        label = f"instance segment {s_i} kind={b.kind}"
+        _assert_truth(got[0][sl], got[1][sl], b.truth, b.t_star, label)
+        e = oracle.err_from_bounds(b.kind, b.verts)
+        assert np.array_equal(segs["err"][s_i], e), label
+        idx = np.sort(rng.choice(b.n, min(b.n, 40), replace=False))
+        o = oracle.ccd_batch(b.kind, b.verts[idx], e, delta=1e-6, max_itr=10**6, nthreads=NT)
+        _assert_parity(tuple(x[sl][idx] for x in got), o, label)
+        off += b.n
