@@ -75,20 +75,26 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=40_000)
     ap.add_argument("--max-itr", type=int, default=10**6,
-                    help="check limit m_I of the simulation-mixed run (profiling cases only)")
+                    help="check limit m_I (smaller values for profiling cases only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--deep-slots", type=int, default=None,
-                    help="cap the deep-solver slots (smaller workspace, e.g. for profiling)")
+    ap.add_argument("--pages", type=int, default=None,
+                    help="simulation-mixed: frontier pages of the deep tier (smaller workspace, "
+                         "e.g. for profiling)")
     ap.add_argument("--workload", default="multi-instance",
                     choices=["simulation-mixed", "multi-instance", "served", "line-search",
                              "active-set"])
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multi-instance/served: fraction of the full query count")
-    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of arrivals")
-    ap.add_argument("--req-scale", type=float, default=0.1,
+    ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
+    ap.add_argument("--req-scale", type=float, default=1.0,
                     help="served: request sizes are log-uniform in [100, 500k] times this")
     ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="multi-instance: the default launch shapes instead of the autotuner's")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="multi-instance: skip the plain-form and simulation-mixed comparisons "
+                         "that follow the timed region (small profiling cases)")
     ap.add_argument("--nx", type=int, default=512, help="active-set: vertices per sheet side")
     ap.add_argument("--compare-printed-cap", action="store_true",
                     help="line-search: also time d = max(p d_i, delta) (about a minute a step)")
@@ -188,9 +194,9 @@ def stage_ops(c: dict, stage: int, n_by_kind: dict) -> tuple[float, float]:
         ops = sum(n * OPS_PER_CHECK[k] for k, n in n_by_kind.items())
         return ops, ops
     if stage == 1:
-        ee = c["evals_pool_ee"]
-        vf = c["evals_pool"] - ee
-        ops = vf * (2 * T_OPS[0] + BOX_OPS[0]) + ee * (2 * T_OPS[1] + BOX_OPS[1])
+        ee, tee = c["evals_pool_ee"], c["tq_pool_ee"]
+        ops = ((c["evals_pool"] - ee) * BOX_OPS[0] + ee * BOX_OPS[1]
+               + (c["tq_pool"] - tee) * T_OPS[0] + tee * T_OPS[1])
         return ops, c["checks_pool"] * max(OPS_PER_CHECK.values())
     if stage == 2:
         tee, eee = c["tq_small_ee"], c["evals_small_ee"]
@@ -246,12 +252,12 @@ def workload_config(args):
             "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0}
 
 
-def multi_config(n_total, scale):
+def multi_config(n_total, scale, max_itr=10**6):
     """The multi-instance workload's config keys, the same for both arms."""
     return {"workload": f"multi-instance: 64 simulation instances, {n_total} queries per GPU "
                         f"(log-uniform 1k-2M each, VF:EE 1:1, per-instance scale 10^U(-2,2) "
                         f"and eps), seed 3" + ("" if scale == 1.0 else f", scale {scale}"),
-            "delta": 1e-6, "max_itr": 10**6, "ms": 0.0}
+            "delta": 1e-6, "max_itr": max_itr, "ms": 0.0}
 
 
 def multi_workload(scale, rank=0):
@@ -325,7 +331,7 @@ def measure_simulation_mixed(args, dev, steps, warmup, seed, stage_detail=True):
     wl = make_workload(args.n, seed)
     batches = wl.batches
     verts = [ccd.to_soa(b.verts, dev) for b in batches]
-    ws = [ccd.workspace(b.n, args.max_itr, dev, deep_slots=args.deep_slots) for b in batches]
+    ws = [ccd.workspace(b.n, args.max_itr, dev, pages=args.pages) for b in batches]
     res = [ccd.Result(torch.empty(b.n, dtype=torch.uint8, device=dev),
                       torch.empty(b.n, dtype=torch.float64, device=dev),
                       torch.empty(b.n, dtype=torch.float64, device=dev),
@@ -555,7 +561,7 @@ def run_multi_instance(args):
         verts[:, off:off + b.n].copy_(t)
         parts.append(t)
         off += b.n
-    seg = ccd.make_segments(counts, kinds, 0.0, 1e-6, 10**6)
+    seg = ccd.make_segments(counts, kinds, 0.0, 1e-6, args.max_itr)
     sd = ccd.segments_to_device(seg, dev)
     s = torch.cuda.Stream(dev)
 
@@ -569,16 +575,20 @@ def run_multi_instance(args):
     ccd.segments_err_from_bounds(sv, ssd)
 
     def measure(t):
-        wst = ccd.multi_workspace(acc, 10**6, t, dev)
+        wst = ccd.multi_workspace(acc, args.max_itr, t, dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        ccd.multi_batch(sv, ssd, 10**6, ws=wst, tuning=t, with_checks=False)
+        ccd.multi_batch(sv, ssd, args.max_itr, ws=wst, tuning=t, with_checks=False)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    tuning, timings = autotune.get_or_tune(_gpu_name(torch, dev), "multi-instance", measure,
-                                           autotune.candidates(sms), reps=1, retune=args.retune)
+    if args.no_tune:
+        tuning, timings = None, None
+    else:
+        tuning, timings = autotune.get_or_tune(_gpu_name(torch, dev), "multi-instance", measure,
+                                               autotune.candidates(sms), reps=1,
+                                               retune=args.retune)
     del sv, ssd
     torch.cuda.empty_cache()
 
@@ -586,20 +596,20 @@ def run_multi_instance(args):
                      torch.empty(n, dtype=torch.float64, device=dev),
                      torch.empty(n, dtype=torch.float64, device=dev),
                      torch.empty(n, dtype=torch.int64, device=dev))
-    ws = ccd.multi_workspace(n, 10**6, tuning, dev)
+    ws = ccd.multi_workspace(n, args.max_itr, tuning, dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     for e in ev:
         e.record(s)                       # creates the handles the library records into
     s.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(s):
         ccd.segments_err_from_bounds(verts, sd, stream=s)
-        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+        ccd.multi_batch(verts, sd, args.max_itr, ws=ws, out=out, tuning=tuning, stream=s)
     s.synchronize()
     g = torch.cuda.CUDAGraph()
     ccd.set_stage_events(ev)              # recorded by the graph at every replay
     with torch.cuda.graph(g, stream=s):
         ccd.segments_err_from_bounds(verts, sd, stream=s)
-        ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+        ccd.multi_batch(verts, sd, args.max_itr, ws=ws, out=out, tuning=tuning, stream=s)
     ccd.set_stage_events(None)
     for _ in range(args.warmup):
         with torch.cuda.stream(s):
@@ -634,7 +644,7 @@ def run_multi_instance(args):
         for i in range(args.steps):
             with torch.cuda.stream(s):
                 ccd.segments_err_from_bounds(verts, sd, stream=s)
-                ccd.multi_batch(verts, sd, 10**6, ws=ws, out=out, tuning=tuning, stream=s)
+                ccd.multi_batch(verts, sd, args.max_itr, ws=ws, out=out, tuning=tuning, stream=s)
             s.synchronize()
             stage_ms[i] = [ev[j].elapsed_time(ev[j + 1]) for j in range(4)]
         ccd.set_stage_events(None)
@@ -673,7 +683,7 @@ def run_multi_instance(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {**multi_config(n, args.scale),
+        "config": {**multi_config(n, args.scale, args.max_itr),
                    "form": "one ccd_multi_batch call (eps per segment + 4 solver stages) "
                            "replayed from a CUDA graph",
                    "tuning": tuning,
@@ -697,7 +707,7 @@ def run_multi_instance(args):
         "counters": counters,
         "checks": {"mean": float(checks.mean()), "p99": float(np.percentile(checks, 99)),
                    "max": int(checks.max()),
-                   "early_termination_pct": float(100.0 * np.mean(checks >= 10**6))},
+                   "early_termination_pct": float(100.0 * np.mean(checks >= args.max_itr))},
         "false_negatives": fn, "toi_after_truth": toi_bad,
         "gpu_launches": args.steps * MULTI_LAUNCHES,
         "paper_context": PAPER_CONTEXT,
@@ -737,14 +747,21 @@ def run_multi_instance(args):
                       "api": "ccd_segments_err_from_bounds + ccd_multi_batch (graph)"}
         del host, out_host
 
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps(res))
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     # the plain form: one eps + batch call per instance-kind, in sequence
-    wsp = ccd.workspace(max(counts), 10**6, dev)
+    wsp = ccd.workspace(max(counts), args.max_itr, dev)
     plain_out = [None] * len(parts)
 
     def plain_step():
         for j, (t, kind) in enumerate(zip(parts, kinds)):
             e = ccd.err_from_bounds(kind, t)
-            plain_out[j] = ccd.batch(kind, t, e, delta=1e-6, max_itr=10**6, ws=wsp,
+            plain_out[j] = ccd.batch(kind, t, e, delta=1e-6, max_itr=args.max_itr, ws=wsp,
                                      out=plain_out[j], with_checks=False)
 
     plain_step()
@@ -807,30 +824,27 @@ def run_multi_instance(args):
 
 
 def run_served(args):
-    """16 clients with Poisson arrivals; request sizes log-uniform in
-    [100, 500k] x --req-scale (uniform unit-cube generator), delta in
-    {1e-4, 1e-6}, ms in {0, 1e-4}, m_I = 1e6; continuous batching on 4 lanes
-    within 40 GB against one call per request, at offered loads 0.7 and 1.2
-    of the capacity measured on the same request mix."""
+    """The served workload: 16 clients with Poisson arrivals; request sizes
+    log-uniform in [100, 500k] x --req-scale (uniform unit-cube generator),
+    delta in {1e-4, 1e-6}, ms in {0, 1e-4}, m_I = 1e6.  The C server
+    (ccd_batch_*: device-resident request queue, admission within a 40 GB
+    arena, 4 lanes, time-sliced deep rounds, a frontier-page pool shared by
+    the lanes) against one call per request (ccd_vf_batch / ccd_ee_batch
+    with eps from the request's bounds, each after the previous one), at
+    offered loads 0.7 and 1.2 of the capacity measured on the same mix."""
     import torch
+    from paper_2009_13349_gb300 import ccd
     from paper_2009_13349_gb300 import workloads as W
-    from paper_2009_13349_gb300.serve import (GpuExecutor, Request, Server, latency_stats,
-                                              run_stream, serial_baseline)
+    from paper_2009_13349_gb300.serve import (Request, Server, latency_stats, run_stream,
+                                              serial_baseline)
     dev = torch.device("cuda", 0)
     lo = max(1, int(round(100 * args.req_scale)))
     hi = max(lo + 1, int(round(500_000 * args.req_scale)))
     pool_n = max(4 * hi, 100_000)
-    pools = {k: torch.from_numpy(W.unit_cube(k, pool_n, seed=40 + k).verts).pin_memory()
-             for k in (0, 1)}
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    # every lane gets the default deep slots (deep blocks fill the SMs, so
-    # lanes take turns); the 40 GB budget bounds the batches in flight
-    tuning = {"deep_threads": 256, "deep_slots": 2 * sms, "small_blocks_per_sm": 16,
-              "small_cap": 1024}
-    serial_tuning = dict(tuning)   # one request at a time: the whole GPU
-    lanes = 4
-    ex = GpuExecutor(lanes, 10**6, tuning, dev)
+    pools = {k: W.unit_cube(k, pool_n, seed=40 + k).verts for k in (0, 1)}
     rng = np.random.default_rng(4)
+    budget = 40 << 30
+    ws_one = ccd.workspace(hi, 10**6, dev)
 
     def draw(i, t):
         size = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
@@ -839,13 +853,21 @@ def run_served(args):
         return Request(i, kind, pools[kind][a:a + size], delta=float(rng.choice([1e-4, 1e-6])),
                        ms=float(rng.choice([0.0, 1e-4])), max_itr=10**6, arrival=t)
 
-    # capacity on the request mix: 32 requests in one batch, after a warm-up
-    mix = [draw(i, 0.0) for i in range(32)]
-    h = ex.launch(0, mix[:4])
-    ex.harvest(h, mix[:4])
+    def run_one(r):
+        """One call for one request: upload, eps, batch, results to the host."""
+        v = ccd.to_soa(r.aos, dev)
+        e = ccd.err_from_bounds(r.kind, v, ms_nonzero=r.ms > 0)
+        o = ccd.batch(r.kind, v, e, ms=r.ms, delta=r.delta, max_itr=r.max_itr, ws=ws_one,
+                      with_checks=False)
+        r.collides, r.toi, r.out_tol = (o.collides.cpu().numpy(), o.toi.cpu().numpy(),
+                                        o.out_tol.cpu().numpy())
+
+    # capacity on the request mix: 24 requests solved one after another
+    mix = [draw(i, 0.0) for i in range(24)]
+    run_one(mix[0])
     t0 = time.perf_counter()
-    h = ex.launch(0, mix)
-    ex.harvest(h, mix)
+    for r in mix:
+        run_one(r)
     cap = sum(r.n for r in mix) / (time.perf_counter() - t0)
     mean_size = (hi - lo) / np.log(hi / lo)
     results = {}
@@ -864,26 +886,27 @@ def run_served(args):
         reqs_a = [draw(i, t) for i, t in enumerate(spec)]
         rng.bit_generator.state = state
         reqs_b = [draw(i, t) for i, t in enumerate(spec)]
-        srv = Server(ex, lanes=lanes, budget=40 << 30, max_batch=1_000_000)
+        srv = Server(budget=budget, lanes=4, max_batch=max(hi, 1 << 20))
         run_stream(srv, reqs_a)
-        serial_baseline(GpuExecutor(1, 10**6, serial_tuning, dev), reqs_b)
+        st = srv.stats()
+        srv.close()
+        serial_baseline(run_one, reqs_b)
         same = all(np.array_equal(a.collides, b.collides) and np.array_equal(a.toi, b.toi)
                    and np.array_equal(a.out_tol, b.out_tol) for a, b in zip(reqs_a, reqs_b))
         results[str(load)] = {"served": latency_stats(reqs_a),
                               "one_call_per_request": latency_stats(reqs_b),
                               "identical": bool(same), "requests": len(spec),
-                              "peak_budget_bytes": srv.peak_bytes,
-                              "batches": srv._next_batch}
+                              "server": st}
     hi_load = results["1.2"]
     print(json.dumps({
         "metric": METRIC, "value": hi_load["served"]["queries_per_s"], "unit": "queries/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"served: 16 Poisson clients, sizes log-uniform {lo}..{hi} "
                                "(unit-cube generator), delta {1e-4,1e-6}, ms {0,1e-4}, m_I 1e6, "
-                               "40 GB budget, 4 lanes",
-                   "duration_s": args.duration, "capacity_queries_per_s": cap,
-                   "tuning": tuning},
+                               "40 GB arena, 4 lanes",
+                   "duration_s": args.duration, "capacity_queries_per_s": cap},
         "loads": results}))
+
 
 def run_line_search(args):
     """One line-search step (Algorithm 4's CCD part) over a candidate set of

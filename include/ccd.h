@@ -41,22 +41,54 @@ typedef enum {
     CCD_ERR_WORKSPACE = -2, /* workspace too small for even one deep slot      */
     CCD_ERR_TIMEOUT = -3,   /* a bounded device wait gave up                   */
     CCD_ERR_CUDA = -4,      /* a CUDA launch or copy failed                    */
-    CCD_ERR_CAPACITY = -5   /* device: a frontier exceeded its slot; the query
+    CCD_ERR_CAPACITY = -5,  /* device: a frontier exceeded its slot; the query
                                was answered conservatively (see ccd_vf_batch)  */
+    CCD_ERR_BUSY = -6,      /* server: no room for the request now; poll and
+                               submit again (or the request is already running)*/
+    CCD_ERR_CANCELLED = -7  /* server: the request was cancelled               */
 } ccd_status;
 
 #define CCD_KIND_VF 0
 #define CCD_KIND_EE 1
 
 /*
- * Bytes of device workspace that ccd_vf_batch / ccd_ee_batch need for n
- * queries at check limit max_itr with the default number of deep slots (three
- * per SM of the current device: a batch runs three deep blocks per SM).  One deep slot takes 48 * (2 * max_itr + 64)
- * bytes.  A smaller workspace is accepted as long as it holds at least one
- * deep slot; fewer slots only reduce parallelism on queries with very large
- * subdivision frontiers.  Returns 0 on bad arguments or without a device.
+ * Workspace of ccd_vf_batch / ccd_ee_batch (n queries, check limit max_itr).
+ * It holds per-query lists, the small-frontier solvers' slots and the deep
+ * tier:
+ *  - a pool of frontier pages (32,768 boxes of 24 bytes = 768 KB each)
+ *    shared by the deep solver's blocks (three per SM): each level of a deep
+ *    query takes pages for its children and frees the previous level's, so
+ *    memory follows the frontiers actually reached;
+ *  - two full-size slots (two arrays of 2 * max_itr + 64 boxes, which no
+ *    level can outgrow: every box of a level is a child of a colliding box
+ *    checked before the limit) for queries that found the pool empty; they
+ *    restart there.
+ * The pool's size therefore changes speed only, never results.
+ * ccd_workspace_bytes gives a pool with, per deep block, pages for one level
+ * of 2 * max_itr + 64 boxes (at least two pages); ccd_workspace_bytes_pages
+ * one of `pages` pages (>= 2).  A workspace too small for one full-size slot
+ * and two pages is used as contiguous slots of fewer boxes, with the
+ * capacity fallback described at ccd_vf_batch.  Both return 0 on bad
+ * arguments or without a device.
  */
 size_t ccd_workspace_bytes(int64_t n, int64_t max_itr);
+size_t ccd_workspace_bytes_pages(int64_t n, int64_t max_itr, int64_t pages);
+
+/* How a workspace of ws_bytes is laid out for n queries at max_itr. */
+typedef struct {
+    int32_t paged;        /* 1: page pool + full-size slots; 0: contiguous slots */
+    int32_t deep_blocks;  /* deep-solver blocks (paged) or slots (contiguous)    */
+    int32_t full_slots;   /* slots of slot_boxes boxes per level                 */
+    int32_t pad;
+    int64_t pages;        /* frontier pages in the pool (paged)                  */
+    int64_t slot_boxes;   /* boxes per level of a slot                           */
+    size_t fixed_bytes;   /* everything before the deep tier                     */
+    size_t used_bytes;    /* bytes of the workspace the layout uses              */
+} ccd_workspace_info;
+
+/* CCD_ERR_WORKSPACE if ws_bytes cannot hold any layout. */
+ccd_status ccd_workspace_layout(int64_t n, int64_t max_itr, size_t ws_bytes,
+                                ccd_workspace_info *info);
 
 /*
  * Batched vertex-face CCD (Algorithm 2 on F_vf, Eq. F-vf; prism-culled
@@ -81,11 +113,12 @@ size_t ccd_workspace_bytes(int64_t n, int64_t max_itr);
  *  workspace, ws_bytes  device scratch (see ccd_workspace_bytes); it must
  *           not be used by another call that may overlap on the device.
  *
- * Results are deterministic and independent of the launch configuration.
- * A query whose frontier does not fit its deep slot (only possible when the
- * workspace holds fewer than 2*max_itr boxes per slot) returns as at the
- * check limit -- collides = 1, toi = left end of the current level's first
- * colliding t-interval -- and the workspace status becomes CCD_ERR_CAPACITY.
+ * Results are deterministic and independent of the launch configuration
+ * and of the workspace's pool size.  Only a workspace too small for a
+ * full-size slot can fall short: a query whose frontier does not fit its
+ * contiguous slot returns as at the check limit -- collides = 1, toi = left
+ * end of the current level's first colliding t-interval -- and the workspace
+ * status becomes CCD_ERR_CAPACITY.
  * Returns CCD_ERR_ARG for n < 0, n >= 2^31, delta <= 0 or NaN, max_itr <= 0,
  * ms < 0 or NaN, err_stride not in {0, 3}, or a NULL array with n > 0;
  * CCD_ERR_WORKSPACE if the workspace is NULL or too small; CCD_ERR_CUDA if a
@@ -145,13 +178,19 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * boxes, [12] deep box evaluations that used the shared partials (all of
  * them), [13] queries the pooled solver handed to
  * the one-warp solver, [14] sum of check counts n of queries finished by
- * the pooled solver, [15] box evaluations executed by the pooled solver
- * (each computes its own t-quantities at t_L and t_R), [16] and [17] the
- * edge-edge parts of [9] and [10], [18] of [15], [19] of [8] and [20] of [5]
- * (the vertex-face part is the difference).  The small-frontier solver of
- * [3], [5], [8] is the one-warp solver.
+ * the pooled solver, [15] box evaluations executed by the pooled solver,
+ * [16] and [17] the edge-edge parts of [9] and [10], [18] of [15], [19] of
+ * [8] and [20] of [5]
+ * (the vertex-face part is the difference), [21] deep queries that found
+ * the page pool empty and restarted in a full-size slot, [22] the most
+ * frontier pages held at once, [23] t-quantity evaluations of the pooled
+ * solver (one per distinct t value of an iteration, shared by that
+ * iteration's boxes), [24] their edge-edge part, [25] iterations of the
+ * pooled solver's warps and [26] the sum over them of the most boxes one
+ * query placed in the iteration.  The small-frontier solver of [3], [5], [8]
+ * is the one-warp solver.
  */
-#define CCD_NUM_COUNTERS 21
+#define CCD_NUM_COUNTERS 27
 ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int32_t count,
                                   void *stream);
 
@@ -421,6 +460,99 @@ ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const double *err
                                int err_stride, double ms, double delta, int64_t max_itr,
                                uint8_t *collides, double *toi, double *out_tol,
                                int64_t *checks, void *stream);
+
+/*
+ * The served form: a request server with continuous batching.
+ *
+ * Clients submit requests -- a set of queries of one kind with their own
+ * delta, ms and m_I (a line search calls CCD with its own d, delta and m_I
+ * every step, Algorithm 4) -- whenever they have them, and poll for the ones
+ * that finished.  The server owns one device arena of budget_bytes, split
+ * into:
+ *  - a device-resident request queue: an inbox ring of query records (the
+ *    request's 24 doubles per query are copied there on submission) and a
+ *    ring of request descriptors;
+ *  - per lane (a CUDA stream) the region of one batch;
+ *  - a pool of deep-frontier pages shared by every lane's deep stage.
+ * Whenever a lane is free, poll() and submit() give it the oldest run of
+ * waiting requests of one cost class (requests with ms > delta subdivide
+ * whole |F| <= ms regions and are batched apart; half of the lanes, at the
+ * higher stream priority, take only the other class), up to max_batch
+ * queries and max_segments requests.  On the lane's stream the batch's
+ * segment table is gathered from the descriptors and its records turned into
+ * planes, on the device; eps comes from each request's own bounds (Eq.
+ * ccd-error / msccd-error over its points, Sec. 6), and the solver stages of
+ * ccd_multi_batch run, the deep stage in rounds of deep_slice_us: a round's
+ * blocks take no new query after the slice, which lets other lanes' kernels
+ * onto the SMs, and poll() starts the next round.  No kernel waits for
+ * anything.  Every request's outputs equal those of ccd_vf_batch /
+ * ccd_ee_batch on its queries alone with eps from its own bounds.
+ *
+ * Requests whose queries do not fit the inbox or the descriptor ring right
+ * now are refused with CCD_ERR_BUSY (submit again after a poll); requests
+ * larger than max_batch, or with max_itr above max_itr_bound, can never run
+ * and are refused with CCD_ERR_ARG.  A waiting request can be cancelled.
+ * One host thread drives a server; it uses the device current at begin.
+ * poll() advances the batches (the next deep round, result copies): call it
+ * at least every deep_slice_us while requests are in flight.
+ */
+typedef struct ccd_server ccd_server;
+
+typedef struct {
+    size_t budget_bytes;     /* device bytes of the arena (default 40 GiB)      */
+    int32_t lanes;           /* batches in flight, 1..16 (default 4)            */
+    int32_t max_requests;    /* requests holding inbox space (default 4096)     */
+    int64_t max_batch;       /* queries per batch and per request (2^20)        */
+    int64_t inbox_queries;   /* inbox capacity in queries (4 * max_batch)       */
+    int32_t max_segments;    /* requests per batch (default 1024)               */
+    int32_t pad;
+    int64_t max_itr_bound;   /* largest m_I a request may ask for (10^6)        */
+    int64_t deep_slice_us;   /* deep round length in microseconds (20,000)      */
+} ccd_server_config;         /* zero fields take the defaults */
+
+typedef struct {
+    int32_t kind;            /* CCD_KIND_VF or CCD_KIND_EE                       */
+    int32_t pad;
+    int64_t n;               /* queries, 0 <= n <= max_batch                     */
+    const double *verts;     /* HOST, n x 24 (query-major, the 24-value order of
+                                the SoA planes); copied during the call         */
+    double ms, delta;        /* minimum separation d >= 0, tolerance delta > 0   */
+    int64_t max_itr;         /* check limit, 1 <= m_I <= max_itr_bound            */
+    uint8_t *collides;       /* HOST outputs, n each, written by the poll that  */
+    double *toi;             /* reports the request                              */
+    double *out_tol;
+    int64_t *checks;         /* HOST, may be NULL                                */
+} ccd_request;
+
+typedef struct {
+    int64_t submitted, completed, cancelled, busy_rejections;
+    int64_t batches, deep_rounds;
+    int64_t inbox_peak_queries;  /* the most inbox records held at once         */
+    int64_t pages;               /* frontier pages in the shared pool           */
+    int32_t pages_peak;          /* the most pages held at once                 */
+    int32_t lanes_busy_peak;     /* the most lanes busy at once                 */
+    size_t arena_bytes;          /* device bytes the server holds               */
+} ccd_server_stats;
+
+/* Creates a server (config may be NULL: all defaults).  CCD_ERR_WORKSPACE
+ * when budget_bytes cannot hold the inbox, the lanes and two pages, or the
+ * arena cannot be allocated. */
+ccd_status ccd_batch_begin(const ccd_server_config *config, ccd_server **server);
+/* Queues a request; *ticket identifies it in poll and cancel. */
+ccd_status ccd_batch_submit(ccd_server *server, const ccd_request *request, int64_t *ticket);
+/* Advances the batches in flight and reports up to cap finished requests
+ * (tickets in done[], their status -- CCD_OK, CCD_ERR_CANCELLED or an error
+ * -- in status[] if not NULL; *ndone of them).  With wait_us > 0 it waits,
+ * bounded by wait_us, until at least one is reported. */
+ccd_status ccd_batch_poll(ccd_server *server, int64_t *done, int32_t *status, int32_t cap,
+                          int32_t *ndone, int32_t wait_us);
+/* Cancels a waiting request (reported by a later poll as CCD_ERR_CANCELLED);
+ * CCD_ERR_BUSY if it already runs (its results will come), CCD_ERR_ARG if the
+ * ticket is unknown or reported. */
+ccd_status ccd_batch_cancel(ccd_server *server, int64_t ticket);
+ccd_status ccd_batch_stats(ccd_server *server, ccd_server_stats *stats);
+/* Waits for the device, then frees everything the server holds. */
+ccd_status ccd_batch_end(ccd_server *server);
 
 /* Static description of a status code. */
 const char *ccd_status_str(int status);

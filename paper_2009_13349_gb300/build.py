@@ -13,7 +13,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc", "ccd.cu")
-SRCS = [SRC, os.path.join(HERE, "csrc", "activeset.cu")]
+SRCS = [SRC, os.path.join(HERE, "csrc", "activeset.cu"), os.path.join(HERE, "csrc", "serve.cu")]
 INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libccd_gb300.so")
@@ -30,7 +30,8 @@ def nvcc() -> str:
 
 
 def sources():
-    return [*SRCS, os.path.join(INCLUDE, "ccd.h")]
+    return [*SRCS, os.path.join(INCLUDE, "ccd.h"), os.path.join(HERE, "csrc", "internal.h"),
+            os.path.join(HERE, "csrc", "serve_queue.h")]
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
@@ -42,7 +43,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     objs, procs = [], []
     for src in SRCS:   # translation units compile in parallel, then one link
         obj = os.path.join(LIB_DIR, os.path.basename(src) + f".{os.getpid()}.o")
-        cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", "-o", obj, src]
+        cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", os.path.join(HERE, "csrc"), "-c",
+               "-o", obj, src]
         if verbose:
             print(" ".join(cmd))
         procs.append((subprocess.Popen(cmd), cmd))

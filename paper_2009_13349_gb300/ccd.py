@@ -18,7 +18,7 @@ from . import build as _build
 
 VF, EE = 0, 1
 STATUS = {0: "CCD_OK", -1: "CCD_ERR_ARG", -2: "CCD_ERR_WORKSPACE", -3: "CCD_ERR_TIMEOUT",
-          -4: "CCD_ERR_CUDA", -5: "CCD_ERR_CAPACITY"}
+          -4: "CCD_ERR_CUDA", -5: "CCD_ERR_CAPACITY", -6: "CCD_ERR_BUSY", -7: "CCD_ERR_CANCELLED"}
 
 _LIB = None
 
@@ -41,6 +41,10 @@ def lib():
         i64, sz = ctypes.c_int64, ctypes.c_size_t
         L.ccd_workspace_bytes.argtypes = [i64, i64]
         L.ccd_workspace_bytes.restype = sz
+        L.ccd_workspace_bytes_pages.argtypes = [i64, i64, i64]
+        L.ccd_workspace_bytes_pages.restype = sz
+        L.ccd_workspace_layout.argtypes = [i64, i64, sz, ctypes.POINTER(WorkspaceInfo)]
+        L.ccd_workspace_layout.restype = ctypes.c_int
         for name in ("ccd_vf_batch", "ccd_ee_batch"):
             f = getattr(L, name)
             f.argtypes = [dp, i64, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, i64,
@@ -93,6 +97,20 @@ def lib():
         L.ccd_fp64_peak_probe.argtypes = [ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_float), vp]
         L.ccd_fp64_peak_probe.restype = ctypes.c_int
+        L.ccd_batch_begin.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.ccd_batch_begin.restype = ctypes.c_int
+        L.ccd_batch_submit.argtypes = [vp, ctypes.POINTER(CRequest), ctypes.POINTER(i64)]
+        L.ccd_batch_submit.restype = ctypes.c_int
+        L.ccd_batch_poll.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.c_int32]
+        L.ccd_batch_poll.restype = ctypes.c_int
+        L.ccd_batch_cancel.argtypes = [vp, i64]
+        L.ccd_batch_cancel.restype = ctypes.c_int
+        L.ccd_batch_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.ccd_batch_stats.restype = ctypes.c_int
+        L.ccd_batch_end.argtypes = [vp]
+        L.ccd_batch_end.restype = ctypes.c_int
         _LIB = L
     return _LIB
 
@@ -123,28 +141,34 @@ def workspace_bytes(n: int, max_itr: int) -> int:
     return int(lib().ccd_workspace_bytes(int(n), int(max_itr)))
 
 
-def deep_slot_bytes(max_itr: int) -> int:
-    """Bytes of one deep-solver slot: two frontiers of 2*max_itr + 64 boxes of
-    24 bytes (the layout documented with ccd_workspace_bytes)."""
-    return 2 * (2 * int(max_itr) + 64) * 24
+PAGE_BOXES = 32768   # boxes per frontier page of the deep tier (768 KB)
 
 
-# deep-solver slots that ccd_workspace_bytes provides per SM (a batch runs
-# three deep blocks per SM)
-DEEP_SLOTS_PER_SM = 3
+class WorkspaceInfo(ctypes.Structure):
+    _fields_ = [("paged", ctypes.c_int32), ("deep_blocks", ctypes.c_int32),
+                ("full_slots", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("pages", ctypes.c_int64), ("slot_boxes", ctypes.c_int64),
+                ("fixed_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t)]
 
 
-def workspace(n: int, max_itr: int, device=None, deep_slots: int | None = None) -> torch.Tensor:
+def workspace_layout(n: int, max_itr: int, ws_bytes: int) -> dict:
+    """ccd_workspace_layout: how a workspace of ws_bytes is used."""
+    info = WorkspaceInfo()
+    _check(lib().ccd_workspace_layout(int(n), int(max_itr), int(ws_bytes), ctypes.byref(info)),
+           "ccd_workspace_layout")
+    return {f: getattr(info, f) for f, _ in WorkspaceInfo._fields_ if f != "pad"}
+
+
+def workspace(n: int, max_itr: int, device=None, pages: int | None = None) -> torch.Tensor:
     """Caller-owned device workspace for ``n`` queries at check limit
-    ``max_itr``; ``deep_slots`` caps the deep-solver slots (default: three
-    per SM)."""
-    nbytes = workspace_bytes(n, max_itr)
+    ``max_itr``; ``pages`` sets the deep tier's frontier pages (default: per
+    deep block, one level of the largest size a level can reach)."""
+    if pages is None:
+        nbytes = workspace_bytes(n, max_itr)
+    else:
+        nbytes = int(lib().ccd_workspace_bytes_pages(int(n), int(max_itr), int(pages)))
     if nbytes == 0:
         raise CCDError(-1, "ccd_workspace_bytes")
-    if deep_slots is not None:
-        dev = torch.device(device or "cuda")
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        nbytes -= max(0, DEEP_SLOTS_PER_SM * sms - int(deep_slots)) * deep_slot_bytes(max_itr)
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
@@ -215,7 +239,8 @@ COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "chec
                  "evals_small", "evals_deep", "status", "tq_small", "tq_deep", "a_tasks_deep",
                  "split_chunks_deep", "evals_shared_deep", "mid_queries", "checks_pool",
                  "evals_pool", "tq_deep_ee", "a_tasks_deep_ee", "evals_pool_ee", "tq_small_ee",
-                 "evals_small_ee")
+                 "evals_small_ee", "deferred_queries", "pages_peak", "tq_pool", "tq_pool_ee",
+                 "pool_iters", "pool_serial")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:
@@ -510,3 +535,75 @@ def to_soa(verts_aos, device="cuda") -> torch.Tensor:
     """(n, 24) host array -> (24, n) contiguous float64 device tensor."""
     t = torch.as_tensor(verts_aos, dtype=torch.float64)
     return t.t().contiguous().to(device)
+
+
+# ---- the served form (ccd_batch_begin / submit / poll / cancel / end) -----------
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("lanes", ctypes.c_int32),
+                ("max_requests", ctypes.c_int32), ("max_batch", ctypes.c_int64),
+                ("inbox_queries", ctypes.c_int64), ("max_segments", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("max_itr_bound", ctypes.c_int64),
+                ("deep_slice_us", ctypes.c_int64)]
+
+
+class CRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("verts", ctypes.c_void_p), ("ms", ctypes.c_double), ("delta", ctypes.c_double),
+                ("max_itr", ctypes.c_int64), ("collides", ctypes.c_void_p),
+                ("toi", ctypes.c_void_p), ("out_tol", ctypes.c_void_p),
+                ("checks", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("busy_rejections", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("deep_rounds", ctypes.c_int64),
+                ("inbox_peak_queries", ctypes.c_int64), ("pages", ctypes.c_int64),
+                ("pages_peak", ctypes.c_int32), ("lanes_busy_peak", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_size_t)]
+
+
+class NativeServer:
+    """Marshalling for the C server: host numpy arrays in and out."""
+
+    def __init__(self, **config):
+        cfg = ServerConfig(**config)
+        h = ctypes.c_void_p()
+        _check(lib().ccd_batch_begin(ctypes.byref(cfg), ctypes.byref(h)), "ccd_batch_begin")
+        self.h = h
+
+    def submit(self, kind, verts_aos: np.ndarray, ms, delta, max_itr, col, toi, tol, chk=None):
+        """Returns the ticket, or None when the server has no room now."""
+        n = int(verts_aos.shape[0])
+        req = CRequest(kind=int(kind), n=n, verts=verts_aos.ctypes.data, ms=float(ms),
+                       delta=float(delta), max_itr=int(max_itr), collides=col.ctypes.data,
+                       toi=toi.ctypes.data, out_tol=tol.ctypes.data,
+                       checks=chk.ctypes.data if chk is not None else None)
+        t = ctypes.c_int64()
+        code = lib().ccd_batch_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if code == -6:
+            return None
+        _check(code, "ccd_batch_submit")
+        return t.value
+
+    def poll(self, cap=256, wait_us=0):
+        done = (ctypes.c_int64 * cap)()
+        st = (ctypes.c_int32 * cap)()
+        nd = ctypes.c_int32()
+        _check(lib().ccd_batch_poll(self.h, done, st, cap, ctypes.byref(nd), int(wait_us)),
+               "ccd_batch_poll")
+        return [(done[i], st[i]) for i in range(nd.value)]
+
+    def cancel(self, ticket) -> int:
+        return lib().ccd_batch_cancel(self.h, int(ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().ccd_batch_stats(self.h, ctypes.byref(s)), "ccd_batch_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().ccd_batch_end(self.h), "ccd_batch_end")
+            self.h = None

@@ -47,6 +47,7 @@
 // extreme corners (corner_range), which give the same bits as all four.
 
 #include "ccd.h"
+#include "internal.h"
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -102,15 +103,24 @@ struct Header {
     unsigned long long evals_pool_ee;   // the part of evals_pool spent on edge-edge queries
     unsigned long long tq_small_ee;     // the part of tq_small spent on edge-edge queries
     unsigned long long evals_small_ee;  // the part of evals_small spent on edge-edge queries
-    int pad[22];
+    int jumbo;        // queries the paged deep solver deferred to the full-size slots
+    int head_jumbo;   // work counter of the full-size (jumbo) stage
+    int pages_used;   // deep frontier pages held now (pools owned by the workspace)
+    int pages_peak;   // the most held at once
+    unsigned long long tq_pool;     // t-quantity evaluations (t values) by the pooled solver
+    unsigned long long tq_pool_ee;  // the part of tq_pool spent on edge-edge queries
+    unsigned long long round_start; // %globaltimer at the start of a time-sliced deep round
+    unsigned long long pool_iters;  // iterations of the pooled solver's warps
+    unsigned long long pool_serial; // sum over those of the most boxes one slot placed
+    int pad[8];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
 struct Layout {
-    size_t off_surv, off_mid, off_over, off_level, off_dlist, off_kappa, off_pool, off_meta, off_small,
-        off_deep, total;
-    int nb_pool, nb_small, nb_deep;
-    long long cap_small, cap_deep;
+    size_t off_surv, off_mid, off_over, off_level, off_dlist, off_jlist, off_kappa, off_pool,
+        off_meta, off_small, off_deep, total;
+    int nb_pool, nb_small;
+    long long cap_small;
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -550,6 +560,7 @@ struct Params {
     int *over;       // one-warp solver hand-offs   -> deep solver
     unsigned char *over_level;   // level at which each hand-off outgrew its slot
     int *deep_list;  // `over` ordered by that level, shallowest first
+    int *jumbo;      // deep queries deferred for lack of frontier pages
     double *kappa;
 };
 
@@ -871,10 +882,183 @@ __device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
     return true;
 }
 
-template <int KIND, int BS>
-__device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur, Box *nxt,
-                            long long cap, bool fallback, Smem<BS> &s, double *tq,
-                            int &hand_level)
+// ---- frontier storage of the level-synchronous solver ---------------------------
+//
+// Contiguous: two arrays of `cap` boxes owned by the block (one-warp slots and
+// the full-size slots, 2 m_I + 64 boxes, which no level can outgrow).
+//
+// Paged (deep tier): the two level arrays are lists of pages of PAGE_BOXES
+// boxes taken from a pool shared by every deep block (of one call, or of all
+// calls of a server): memory follows the frontiers actually reached instead
+// of the worst case.  Before building a level the block reserves pages for
+// 2 ncol children (the most a level of ncol colliding boxes can have) and
+// afterwards frees the consumed level and the surplus.  Pages are taken from
+// a free bitmap with bounded scans and atomics; nothing waits.  A query that
+// cannot get pages is handed back (the caller defers it to a full-size slot,
+// where it restarts), so the pool's size changes speed, never results.
+constexpr int PAGE_SHIFT = 15;
+constexpr long long PAGE_BOXES = 1LL << PAGE_SHIFT;   // 768 KB of boxes
+constexpr long long PAGE_MASK = PAGE_BOXES - 1;
+constexpr int PT_CAP = 128;                           // pages per level (4.19M boxes)
+
+struct PagePool {
+    Box *base;                  // npages pages
+    unsigned long long *bits;   // bit set = page free (bits past npages stay clear)
+    int nwords;
+    int *used, *peak;           // pages held now / at most (may be null)
+};
+
+struct PageTables {             // one deep block's page lists (shared memory)
+    int pt[2][PT_CAP];
+    int got;
+};
+
+template <int BS>
+struct ContigFrontier {
+    Box *cur, *nxt;
+    long long cap;
+    __device__ __forceinline__ bool init() { return true; }
+    __device__ __forceinline__ Box &c(long long i) const { return cur[i]; }
+    __device__ __forceinline__ Box &x(long long i) const { return nxt[i]; }
+    __device__ __forceinline__ long long room(long long) const { return cap; }
+    __device__ __forceinline__ void swap(long long)
+    {
+        bsync<BS>();
+        Box *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    __device__ __forceinline__ void release() {}
+};
+
+// Frees entries [from, to) of page list t (called after a barrier: every
+// read of those pages is done).  Each freeing thread fences first, so the
+// block's writes to a page are visible before another block can take it.
+template <int BS>
+__device__ __noinline__ void pages_give(const PagePool &P, PageTables *T, int t, int from, int to)
+{
+    for (int i = from + (int)threadIdx.x; i < to; i += BS) {
+        const int pg = T->pt[t][i];
+        __threadfence();
+        atomicOr(&P.bits[pg >> 6], 1ull << (pg & 63));
+    }
+    if (threadIdx.x == 0 && P.used && to > from) atomicSub(P.used, to - from);
+}
+
+// Takes `want` pages into page list t; every thread of the block calls it.
+// Warp 0 scans the bitmap from a block-dependent word, each lane over its
+// own words, clearing set bits with atomicAnd (a bit it cleared is a page
+// taken); every loop is bounded.  On failure the pages taken are returned.
+template <int BS>
+__device__ __noinline__ bool pages_take(const PagePool &P, PageTables *T, int t, int want)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) T->got = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, nw = P.nwords;
+        const int s0 = (int)(((unsigned)blockIdx.x * 2654435761u) % (unsigned)nw);
+        for (int k = lane; k < nw; k += 32) {
+            if (*(volatile int *)&T->got >= want) break;
+            int w = s0 + k;
+            if (w >= nw) w -= nw;
+            unsigned long long v = *(volatile unsigned long long *)&P.bits[w];
+            for (int tries = 0; v != 0ull && tries < 128; ++tries) {
+                const int b = __ffsll((long long)v) - 1;
+                const unsigned long long m = 1ull << b;
+                const unsigned long long old = atomicAnd(&P.bits[w], ~m);
+                if (old & m) {
+                    const int slot = atomicAdd(&T->got, 1);
+                    if (slot < want) T->pt[t][slot] = w * 64 + b;
+                    else { atomicOr(&P.bits[w], m); break; }
+                }
+                if (*(volatile int *)&T->got >= want) break;
+                v = old & ~m;
+            }
+        }
+    }
+    __syncthreads();
+    const int got = min(T->got, want);
+    if (got < want) {
+        for (int i = (int)threadIdx.x; i < got; i += BS) {
+            const int pg = T->pt[t][i];
+            atomicOr(&P.bits[pg >> 6], 1ull << (pg & 63));
+        }
+        return false;
+    }
+    if (threadIdx.x == 0 && P.used) {
+        const int u = atomicAdd(P.used, want) + want;
+        if (P.peak) atomicMax(P.peak, u);
+    }
+    return true;
+}
+
+template <int BS>
+struct PagedFrontier {
+    const PagePool &P;
+    PageTables *T;
+    int ic = 0;               // page list of the current level
+    int ncur = 0, nnxt = 0;   // pages held (block-uniform)
+
+    __device__ __forceinline__ Box &c(long long i) const
+    {
+        return P.base[((size_t)T->pt[ic][i >> PAGE_SHIFT] << PAGE_SHIFT) | (size_t)(i & PAGE_MASK)];
+    }
+    __device__ __forceinline__ Box &x(long long i) const
+    {
+        return P.base[((size_t)T->pt[ic ^ 1][i >> PAGE_SHIFT] << PAGE_SHIFT) |
+                      (size_t)(i & PAGE_MASK)];
+    }
+    __device__ __forceinline__ bool init()
+    {
+        ic = 0;
+        ncur = nnxt = 0;
+        if (!pages_take<BS>(P, T, 0, 1)) return false;
+        ncur = 1;
+        return true;
+    }
+    // room for the children of ncol colliding boxes, or -1 without pages
+    __device__ __forceinline__ long long room(long long ncol)
+    {
+        const long long want = (2 * ncol + PAGE_BOXES - 1) >> PAGE_SHIFT;
+        if (want > PT_CAP || !pages_take<BS>(P, T, ic ^ 1, (int)want)) return -1;
+        nnxt = (int)want;
+        return want << PAGE_SHIFT;
+    }
+    __device__ __forceinline__ void swap(long long nchild)
+    {
+        __syncthreads();   // every read of the current level is done
+        const int keep = (int)((nchild + PAGE_BOXES - 1) >> PAGE_SHIFT);
+        pages_give<BS>(P, T, ic, 0, ncur);
+        pages_give<BS>(P, T, ic ^ 1, keep, nnxt);
+        ncur = keep;
+        nnxt = 0;
+        ic ^= 1;
+        __syncthreads();
+    }
+    __device__ __forceinline__ void release()
+    {
+        __syncthreads();
+        pages_give<BS>(P, T, ic, 0, ncur);
+        pages_give<BS>(P, T, ic ^ 1, 0, nnxt);
+        ncur = nnxt = 0;
+        __syncthreads();
+    }
+};
+
+// Marks the pool's npages pages free (bits past npages stay clear).
+__global__ void pool_init_kernel(unsigned long long *bits, int nwords, int npages)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    const int lo = w * 64;
+    const int k = npages - lo >= 64 ? 64 : (npages - lo > 0 ? npages - lo : 0);
+    bits[w] = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+}
+
+template <int KIND, int BS, class FR>
+__device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, bool fallback,
+                            Smem<BS> &s, double *tq, int &hand_level)
 {
     const int tid = threadIdx.x;
     unsigned long long evals = 0;   // boxes evaluated (thread 0's tally)
@@ -895,7 +1079,11 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
     constexpr int W = TWidth<KIND>::W;
     int k[3] = {0, 0, 0};
     long long size = 1;
-    if (tid == 0) cur[0] = Box{{0ull, 0ull, 0ull}};
+    if (!F.init()) {                 // no frontier page: deferred
+        hand_level = -1;
+        return false;
+    }
+    if (tid == 0) F.c(0) = Box{{0ull, 0ull, 0ull}};
     bsync<BS>();
     long long n_before = 0;
 
@@ -922,7 +1110,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             const bool valid = i < size;
             Box b = Box{{0ull, 0ull, 0ull}};
             BoxTest bt{false, false, 0.0};
-            if (valid) b = cur[i];
+            if (valid) b = F.c(i);
             if (BS > 32) {
                 // the whole chunk, else its sub-chunks in turn (block-uniform;
                 // a sub-chunk always fits, so each pass makes progress)
@@ -1002,9 +1190,10 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                         if (tid == 0) {
                             write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])), first_w,
                                          nfc);
-                            count_done<KIND>(p, fallback, nfc, evals, tqs, atasks, split_chunks,
+                            count_done<KIND>(p, BS > 32, nfc, evals, tqs, atasks, split_chunks,
                                        shared_evals);
                         }
+                        F.release();
                         return true;
                     }
                 }
@@ -1013,12 +1202,13 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     if (tid == 0) {
                         write_result(p, qi, 1, dmul(q.t_max, dyadic(if_at, k[0])),
                                      s.dec[wc].w_cut, ncut);
-                        count_done<KIND>(p, fallback, ncut, evals, tqs, atasks, split_chunks, shared_evals);
+                        count_done<KIND>(p, BS > 32, ncut, evals, tqs, atasks, split_chunks, shared_evals);
                     }
+                    F.release();
                     return true;
                 }
                 const int pre = before + __popc(mh & ((1u << lane) - 1u));
-                if (bt.hit) cur[ncol + pre] = b;   // in-place compaction, ncol + pre <= i
+                if (bt.hit) F.c(ncol + pre) = b;   // in-place compaction, ncol + pre <= i
                 ncol += total;
             }
             bsync<BS>();
@@ -1027,13 +1217,21 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (tid == 0) {
                 write_result(p, qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                              n_before + size);
-                count_done<KIND>(p, fallback, n_before + size, evals, tqs, atasks, split_chunks, shared_evals);
+                count_done<KIND>(p, BS > 32, n_before + size, evals, tqs, atasks, split_chunks, shared_evals);
             }
+            F.release();
             return true;
         }
         n_before += size;
 
         // children of the ncol colliding boxes, in Q order
+        const long long cap = F.room(ncol);
+        if (cap < 0) {                  // no pages for the next level: deferred
+            if (tid == 0) count_done<KIND>(p, true, 0, evals, tqs, atasks, split_chunks, shared_evals);
+            F.release();
+            hand_level = -1;
+            return false;
+        }
         long long nchild;
         if (sd == 0) {
             nchild = 2 * ncol;
@@ -1045,11 +1243,11 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     Box b = Box{{0ull, 0ull, 0ull}};
                     long long v = -1;
                     if (valid) {
-                        b = cur[j];
-                        if (j == 0 || cur[j - 1].a[0] != b.a[0]) v = j;
+                        b = F.c(j);
+                        if (j == 0 || F.c(j - 1).a[0] != b.a[0]) v = j;
                     }
                     const long long gs = max(carry, block_incl_maxscan<BS>(v, s));
-                    if (valid) nxt[j + gs] = Box{{2 * b.a[0], b.a[1], b.a[2]}};
+                    if (valid) F.x(j + gs) = Box{{2 * b.a[0], b.a[1], b.a[2]}};
                     carry = max(carry, block_maxl<BS>(v, s));
                 }
                 long long carry_e = ncol;   // end of the open group, scanning backwards
@@ -1060,11 +1258,11 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                     Box b = Box{{0ull, 0ull, 0ull}};
                     long long v = BIGL;
                     if (valid) {
-                        b = cur[j];
-                        if (j + 1 == ncol || cur[j + 1].a[0] != b.a[0]) v = j + 1;
+                        b = F.c(j);
+                        if (j + 1 == ncol || F.c(j + 1).a[0] != b.a[0]) v = j + 1;
                     }
                     const long long ge = min(carry_e, block_suffix_min<BS>(v, s));
-                    if (valid) nxt[j + ge] = Box{{2 * b.a[0] + 1, b.a[1], b.a[2]}};
+                    if (valid) F.x(j + ge) = Box{{2 * b.a[0] + 1, b.a[1], b.a[2]}};
                     carry_e = min(carry_e, block_minl<BS>(v, s));
                 }
             }
@@ -1076,7 +1274,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 Box b = Box{{0ull, 0ull, 0ull}};
                 bool keep_r = false;
                 if (valid) {
-                    b = cur[j];
+                    b = F.c(j);
                     keep_r = true;
                     if (KIND == CCD_KIND_VF) {
                         // right child meets the prism iff u_L + v_L <= 1 (exact)
@@ -1102,8 +1300,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                         l.a[sd] = 2 * b.a[sd];
                         r.a[sd] = 2 * b.a[sd] + 1;
                     }
-                    if (pos < cap) nxt[pos] = l;
-                    if (keep_r && pos + 1 < cap) nxt[pos + 1] = r;
+                    if (pos < cap) F.x(pos) = l;
+                    if (keep_r && pos + 1 < cap) F.x(pos + 1) = r;
                 }
                 carry += total;
             }
@@ -1113,6 +1311,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
             if (!fallback) {
                 if (tid == 0) count_done<KIND>(p, false, 0, evals, tqs);
                 hand_level = k[0] + k[1] + k[2];
+                F.release();
                 return false;
             }
             // answered as at the check limit: conservative, flagged
@@ -1122,12 +1321,10 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
                 atomicAdd(&p.hdr->fallbacks, 1);
                 count_done<KIND>(p, true, n_before, evals, tqs, atasks, split_chunks, shared_evals);
             }
+            F.release();
             return true;
         }
-        bsync<BS>();
-        Box *t = cur;
-        cur = nxt;
-        nxt = t;
+        F.swap(nchild);
         size = nchild;
         if (BS > 32) {
 #pragma unroll
@@ -1142,9 +1339,12 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, Box *cur
 // *head); a query whose frontier outgrows `cap` goes to out_list, with the
 // level it reached in out_level when that is not null (one-warp tier only;
 // the deep tier answers it through the capacity fallback).
-template <int KIND, int BS>
+//
+// PAGED (deep tier): frontier pages come from `pool`; a query that cannot get
+// them goes to out_list (the full-size stage), where it restarts.
+template <int KIND, int BS, bool PAGED = false>
 __global__ void __launch_bounds__(BS, BS == 256 ? DEEP_BLOCKS_PER_SM : 1)
-    solve_kernel(Params p, int deep, Box *slots, long long cap, const int *list,
+    solve_kernel(Params p, int deep, Box *slots, long long cap, PagePool pool, const int *list,
                  const int *count, int *head, int *out_list, unsigned char *out_level,
                  int *out_count)
 {
@@ -1161,9 +1361,16 @@ __global__ void __launch_bounds__(BS, BS == 256 ? DEEP_BLOCKS_PER_SM : 1)
         if (idx >= *(volatile const int *)count) return;
         const long long qi = list[idx];
         int level = 0;
-        const bool done = solve_query<KIND, BS>(p, qp_single(p, qi), qi, cur, nxt, cap, deep != 0,
-                                                s, tq, level);
-        if (!done && threadIdx.x == 0) {
+        bool done;
+        if constexpr (PAGED) {
+            __shared__ PageTables pt;
+            PagedFrontier<BS> F{pool, &pt};
+            done = solve_query<KIND, BS>(p, qp_single(p, qi), qi, F, false, s, tq, level);
+        } else {
+            ContigFrontier<BS> F{cur, nxt, cap};
+            done = solve_query<KIND, BS>(p, qp_single(p, qi), qi, F, deep != 0, s, tq, level);
+        }
+        if (!done && threadIdx.x == 0 && out_count) {
             const int j = atomicAdd(out_count, 1);
             out_list[j] = (int)qi;
             if (out_level) out_level[j] = (unsigned char)level;
@@ -1304,7 +1511,7 @@ __global__ void __launch_bounds__(32)
     Box *const mine = mem + ((size_t)blockIdx.x * POOL_SLOTS + lane) * 3 * (size_t)cap;
     const int count = *(volatile const int *)count_p;
     bool drained = false;
-    unsigned long long evals = 0, checks_done = 0;
+    unsigned long long evals = 0, checks_done = 0, tqs = 0, iters = 0, serial = 0;
     int rot = 0;
     S.qi = -1;
     __syncwarp();
@@ -1382,6 +1589,8 @@ __global__ void __launch_bounds__(32)
         // the corners of its box from them.
         const int nbox = min(total, 32);
         const bool have = lane < nbox;
+        iters += 1;
+        serial += (unsigned long long)__reduce_max_sync(FULL, (unsigned)take);
         BoxTest bt{false, false, 0.0};
         Box b = Box{{0ull, 0ull, 0ull}};
         int so = 0;
@@ -1410,6 +1619,7 @@ __global__ void __launch_bounds__(32)
         const int tl = (pk & 0xff) - 1 + (pk >> 8);
         const int last = __shfl_sync(FULL, pk, 31);
         const int ntv = nbox > 0 ? (last & 0xff) + (last >> 8) + 1 : 0;
+        tqs += (unsigned long long)ntv;   // warp-uniform: every lane's tally is the warp's
         if (start) { sh.tv_slot[tl] = so; sh.tv_a[tl] = at; }
         if (open_r) { sh.tv_slot[tl + 1] = so; sh.tv_a[tl + 1] = at + 1; }
         __syncwarp();
@@ -1526,6 +1736,12 @@ __global__ void __launch_bounds__(32)
     }
     atomicAdd(&p.hdr->evals_pool, evals);
     if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->evals_pool_ee, evals);
+    if (lane == 0) {
+        atomicAdd(&p.hdr->tq_pool, tqs);
+        if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->tq_pool_ee, tqs);
+        atomicAdd(&p.hdr->pool_iters, iters);
+        atomicAdd(&p.hdr->pool_serial, serial);
+    }
     atomicAdd(&p.hdr->checks_pool, checks_done);
 }
 
@@ -1570,21 +1786,46 @@ __global__ void __launch_bounds__(ROOT_THREADS)
     else root_query<CCD_KIND_EE>(p, i, q);
 }
 
-template <int BS>
+// deep: 0 = one-warp stage (list `mid`), 1 = deep stage (deep_list; PAGED:
+// frontier pages from `pool`, queries without pages deferred to `jumbo`),
+// 2 = full-size stage (the deferred queries).
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// slice_ns > 0 (deep stage of a served batch): the round ends slice_ns after
+// its first block started; a block takes no new query after that, so the SMs
+// come free for other batches' kernels, and the host launches another round
+// for the queries left in the list (no query is interrupted).
+template <int BS, bool PAGED = false>
 __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
-                     long long cap)
+                     long long cap, PagePool pool, long long slice_ns = 0)
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
+    __shared__ unsigned long long s_t0;
     extern __shared__ double tq[];   // [2 * BS][TWidth<EE>::W]: sized for either kind
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
-    const int *list = deep ? p.deep_list : p.mid;
-    const int *count = deep ? &p.hdr->overflow : &p.hdr->mid;
-    int *head = deep ? &p.hdr->head_deep : &p.hdr->head_small;
+    const int *list = deep == 2 ? p.jumbo : deep ? p.deep_list : p.mid;
+    const int *count = deep == 2 ? &p.hdr->jumbo : deep ? &p.hdr->overflow : &p.hdr->mid;
+    int *head = deep == 2 ? &p.hdr->head_jumbo : deep ? &p.hdr->head_deep : &p.hdr->head_small;
+    if (slice_ns > 0 && threadIdx.x == 0) {
+        const unsigned long long now = global_ns();
+        const unsigned long long t0 = atomicCAS(&p.hdr->round_start, 0ull, now);
+        s_t0 = t0 ? t0 : now;
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(head, 1);
+        if (threadIdx.x == 0) {
+            if (slice_ns > 0 && global_ns() - s_t0 > (unsigned long long)slice_ns)
+                s_idx = 0x7fffffff;   // the round is over: leave the rest for the next one
+            else
+                s_idx = atomicAdd(head, 1);
+        }
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
@@ -1593,14 +1834,27 @@ __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
         const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
         const QP q = qp_segment(sg);
         int level = 0;
-        const bool done =
-            sg.kind == CCD_KIND_VF
-                ? solve_query<CCD_KIND_VF, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq, level)
-                : solve_query<CCD_KIND_EE, BS>(p, q, qi, cur, nxt, cap, deep != 0, s, tq, level);
+        bool done;
+        if constexpr (PAGED) {
+            __shared__ PageTables pt;
+            PagedFrontier<BS> F{pool, &pt};
+            done = sg.kind == CCD_KIND_VF
+                       ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, false, s, tq, level)
+                       : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, false, s, tq, level);
+        } else {
+            ContigFrontier<BS> F{cur, nxt, cap};
+            done = sg.kind == CCD_KIND_VF
+                       ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, deep != 0, s, tq, level)
+                       : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, deep != 0, s, tq, level);
+        }
         if (!done && threadIdx.x == 0) {
-            const int j = atomicAdd(&p.hdr->overflow, 1);
-            p.over[j] = (int)qi;
-            p.over_level[j] = (unsigned char)level;
+            if (deep) {                  // paged deep stage: deferred to a full-size slot
+                p.jumbo[atomicAdd(&p.hdr->jumbo, 1)] = (int)qi;
+            } else {
+                const int j = atomicAdd(&p.hdr->overflow, 1);
+                p.over[j] = (int)qi;
+                p.over_level[j] = (unsigned char)level;
+            }
         }
         __syncthreads();
     }
@@ -1980,6 +2234,7 @@ Layout layout_fixed(long long n, int sms)
     L.off_over = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_level = off; off = align256(off + (size_t)n);
     L.off_dlist = off; off = align256(off + sizeof(int) * (size_t)n);
+    L.off_jlist = off; off = align256(off + sizeof(int) * (size_t)n);
     L.off_kappa = off; off = align256(off + 3 * sizeof(double) * (size_t)n);
     L.nb_pool = sms * POOL_BLOCKS_PER_SM;
     L.off_pool = off;
@@ -1994,26 +2249,101 @@ Layout layout_fixed(long long n, int sms)
     return L;
 }
 
-bool layout_for(long long n, long long max_itr, size_t ws_bytes, int sms, Layout *out)
+// ---- the deep tier's part of a workspace -------------------------------------
+//
+// Paged: J full-size slots (two arrays of 2 m_I + 64 boxes each, for the
+// queries the deep stage defers), a free bitmap and a pool of frontier pages
+// shared by the deep blocks.  Contiguous (only when the room cannot hold one
+// full-size slot and two pages): as many slots as fit, each of `cap` boxes
+// per level; a level beyond it is answered by the capacity fallback.
+constexpr size_t PAGE_BYTES = sizeof(Box) * (size_t)PAGE_BOXES;
+constexpr int JUMBO_SLOTS = 2;
+
+struct DeepLayout {
+    bool paged;
+    int nb_deep;                  // deep blocks (paged) / contiguous slots
+    long long cap_deep;           // boxes per level of a contiguous or full-size slot
+    int nb_jumbo;                 // full-size slots (paged)
+    size_t off_slots;             // contiguous or full-size slots
+    size_t off_bits, off_pages;   // paged
+    int nwords;
+    long long npages;
+    size_t total;
+};
+
+long long pages_for(long long boxes) { return (boxes + PAGE_BOXES - 1) / PAGE_BOXES; }
+
+// Pages a default workspace provides: for every deep block one level of the
+// largest size any level can reach (2 m_I boxes), and at least two.
+long long default_pages(long long nb_deep, long long max_itr)
 {
-    Layout L = layout_fixed(n, sms);
-    if (ws_bytes < L.off_deep) return false;
-    const size_t room = ws_bytes - L.off_deep;
-    const long long want = deep_cap(max_itr);
-    const size_t per = sizeof(Box) * 2 * (size_t)want;
-    long long nb = (long long)(room / per);
-    if (nb >= 1) {
-        const long long most = (long long)DEEP_BLOCKS_PER_SM * sms;
-        L.nb_deep = (int)(nb < most ? nb : most);
-        L.cap_deep = want;
-    } else {
-        L.nb_deep = 1;
-        L.cap_deep = (long long)(room / (sizeof(Box) * 2));
-        if (L.cap_deep < 1024) return false;
+    long long per = pages_for(deep_cap(max_itr));
+    return nb_deep * (per < 2 ? 2 : per);
+}
+
+size_t pool_bytes(long long npages)
+{
+    return align256(sizeof(unsigned long long) * (size_t)((npages + 63) / 64)) +
+           PAGE_BYTES * (size_t)npages;
+}
+
+bool deep_layout(size_t off, size_t ws_bytes, long long max_itr, int nb_deep_max, DeepLayout *D)
+{
+    if (ws_bytes < off) return false;
+    const size_t room = ws_bytes - off;
+    const size_t slot = align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr));
+    DeepLayout d{};
+    d.off_slots = off;
+    d.cap_deep = deep_cap(max_itr);
+    for (int J = JUMBO_SLOTS; J >= 1; --J) {
+        if (room < J * slot + 256 + 2 * PAGE_BYTES) continue;
+        const size_t rest = room - J * slot;
+        long long np = (long long)(rest / PAGE_BYTES);
+        const size_t bits = align256(sizeof(unsigned long long) * (size_t)((np + 63) / 64));
+        np = (long long)((rest - bits) / PAGE_BYTES);
+        if (np > (1LL << 30)) np = 1LL << 30;
+        if (np < 2) continue;
+        d.paged = true;
+        d.nb_deep = nb_deep_max;
+        d.nb_jumbo = J;
+        d.off_bits = off + J * slot;
+        d.nwords = (int)((np + 63) / 64);
+        d.off_pages = d.off_bits + align256(sizeof(unsigned long long) * (size_t)d.nwords);
+        d.npages = np;
+        d.total = d.off_pages + PAGE_BYTES * (size_t)np;
+        *D = d;
+        return true;
     }
-    L.total = L.off_deep + sizeof(Box) * 2 * (size_t)L.cap_deep * L.nb_deep;
-    *out = L;
+    const long long nb = (long long)(room / slot);
+    if (nb >= 1) {
+        d.nb_deep = (int)(nb < nb_deep_max ? nb : nb_deep_max);
+    } else {
+        d.nb_deep = 1;
+        d.cap_deep = (long long)(room / (sizeof(Box) * 2));
+        if (d.cap_deep < 1024) return false;
+    }
+    d.total = off + sizeof(Box) * 2 * (size_t)d.cap_deep * d.nb_deep;
+    *D = d;
     return true;
+}
+
+size_t default_deep_bytes(long long max_itr, int nb_deep)
+{
+    return JUMBO_SLOTS * align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr)) +
+           pool_bytes(default_pages(nb_deep, max_itr));
+}
+
+PagePool make_pool(char *ws, const DeepLayout &D, Header *h)
+{
+    PagePool pool{};
+    if (D.paged) {
+        pool.base = (Box *)(ws + D.off_pages);
+        pool.bits = (unsigned long long *)(ws + D.off_bits);
+        pool.nwords = D.nwords;
+        pool.used = &h->pages_used;
+        pool.peak = &h->pages_peak;
+    }
+    return pool;
 }
 
 cudaEvent_t g_stage_events[5];
@@ -2045,8 +2375,10 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     if (!workspace) return CCD_ERR_WORKSPACE;
     const int sms = device_sms();
     if (sms <= 0) return CCD_ERR_CUDA;
-    Layout L;
-    if (!layout_for(n, max_itr, ws_bytes, sms, &L)) return CCD_ERR_WORKSPACE;
+    const Layout L = layout_fixed(n, sms);
+    DeepLayout D;
+    if (!deep_layout(L.off_deep, ws_bytes, max_itr, DEEP_BLOCKS_PER_SM * sms, &D))
+        return CCD_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)workspace;
     if (cudaMemsetAsync(ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
@@ -2062,11 +2394,16 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     p.over = (int *)(ws + L.off_over);
     p.over_level = (unsigned char *)(ws + L.off_level);
     p.deep_list = (int *)(ws + L.off_dlist);
+    p.jumbo = (int *)(ws + L.off_jlist);
     p.kappa = (double *)(ws + L.off_kappa);
     Header *h = p.hdr;
+    const PagePool pool = make_pool(ws, D, h);
 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
     stage_mark(0, st);
+    if (D.paged)
+        pool_init_kernel<<<(D.nwords + 255) / 256, 256, 0, st>>>(pool.bits, D.nwords,
+                                                                 (int)D.npages);
     root_kernel<KIND><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     stage_mark(1, st);
     const int nb_pool = pool_blocks(pool_kernel<KIND>, sms);
@@ -2076,29 +2413,43 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
     const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared partials
-    if (cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(solve_kernel<KIND, DEEP_THREADS>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-        return CCD_ERR_CUDA;
+    auto *deep_paged = solve_kernel<KIND, DEEP_THREADS, true>;
+    auto *deep_contig = solve_kernel<KIND, DEEP_THREADS, false>;
+    for (auto *k : {deep_paged, deep_contig})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+                cudaSuccess)
+            return CCD_ERR_CUDA;
+    int nb_deep = D.nb_deep;
     {   // resident deep blocks per SM: the persistent grid must fit at once
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<KIND, DEEP_THREADS>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, D.paged ? deep_paged : deep_contig,
                                                           DEEP_THREADS, tq_deep) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         if (per_sm > DEEP_BLOCKS_PER_SM) per_sm = DEEP_BLOCKS_PER_SM;
-        if (L.nb_deep > per_sm * sms) L.nb_deep = per_sm * sms;
+        if (nb_deep > per_sm * sms) nb_deep = per_sm * sms;
     }
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
-        p, 0, (Box *)(ws + L.off_small), L.cap_small, p.mid, &h->mid, &h->head_small, p.over,
-        p.over_level, &h->overflow);
+        p, 0, (Box *)(ws + L.off_small), L.cap_small, PagePool{}, p.mid, &h->mid, &h->head_small,
+        p.over, p.over_level, &h->overflow);
     order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &h->overflow, p.deep_list);
     stage_mark(3, st);
-    solve_kernel<KIND, DEEP_THREADS><<<L.nb_deep, DEEP_THREADS, tq_deep, st>>>(
-        p, 1, (Box *)(ws + L.off_deep), L.cap_deep, p.deep_list, &h->overflow, &h->head_deep,
-        nullptr, nullptr, nullptr);
+    if (D.paged) {
+        // deep queries on frontier pages; those that find no pages restart
+        // in the full-size slots
+        deep_paged<<<nb_deep, DEEP_THREADS, tq_deep, st>>>(
+            p, 1, nullptr, 0, pool, p.deep_list, &h->overflow, &h->head_deep, p.jumbo, nullptr,
+            &h->jumbo);
+        deep_contig<<<D.nb_jumbo, DEEP_THREADS, tq_deep, st>>>(
+            p, 1, (Box *)(ws + D.off_slots), D.cap_deep, PagePool{}, p.jumbo, &h->jumbo,
+            &h->head_jumbo, nullptr, nullptr, nullptr);
+    } else {
+        deep_contig<<<nb_deep, DEEP_THREADS, tq_deep, st>>>(
+            p, 1, (Box *)(ws + D.off_slots), D.cap_deep, PagePool{}, p.deep_list, &h->overflow,
+            &h->head_deep, nullptr, nullptr, nullptr);
+    }
     stage_mark(4, st);
     if (cudaGetLastError() != cudaSuccess) return CCD_ERR_CUDA;
     return CCD_OK;
@@ -2113,9 +2464,8 @@ size_t ccd_workspace_bytes(int64_t n, int64_t max_itr)
     if (n < 0 || n >= 0x7fffffffLL || max_itr <= 0) return 0;
     const int sms = device_sms();
     if (sms <= 0) return 0;
-    Layout L = layout_fixed(n, sms);
-    return L.off_deep +
-           sizeof(Box) * 2 * (size_t)deep_cap(max_itr) * (size_t)(DEEP_BLOCKS_PER_SM * sms);
+    const Layout L = layout_fixed(n, sms);
+    return L.off_deep + default_deep_bytes(max_itr, DEEP_BLOCKS_PER_SM * sms);
 }
 
 ccd_status ccd_vf_batch(const double *verts, int64_t n, const double *err, int err_stride,
@@ -2134,6 +2484,36 @@ ccd_status ccd_ee_batch(const double *verts, int64_t n, const double *err, int e
 {
     return run_batch<CCD_KIND_EE>(verts, n, err, err_stride, ms, delta, max_itr, collides, toi,
                                   out_tol, checks, workspace, ws_bytes, stream);
+}
+
+size_t ccd_workspace_bytes_pages(int64_t n, int64_t max_itr, int64_t pages)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr <= 0 || pages < 2 || pages > (1LL << 30)) return 0;
+    const int sms = device_sms();
+    if (sms <= 0) return 0;
+    const Layout L = layout_fixed(n, sms);
+    return L.off_deep + JUMBO_SLOTS * align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr)) +
+           pool_bytes(pages);
+}
+
+ccd_status ccd_workspace_layout(int64_t n, int64_t max_itr, size_t ws_bytes,
+                                ccd_workspace_info *info)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr <= 0 || !info) return CCD_ERR_ARG;
+    const int sms = device_sms();
+    if (sms <= 0) return CCD_ERR_CUDA;
+    const Layout L = layout_fixed(n, sms);
+    DeepLayout D;
+    if (!deep_layout(L.off_deep, ws_bytes, max_itr, DEEP_BLOCKS_PER_SM * sms, &D))
+        return CCD_ERR_WORKSPACE;
+    info->paged = D.paged ? 1 : 0;
+    info->deep_blocks = D.nb_deep;
+    info->full_slots = D.paged ? D.nb_jumbo : D.nb_deep;
+    info->pages = D.paged ? D.npages : 0;
+    info->slot_boxes = D.cap_deep;
+    info->fixed_bytes = L.off_deep;
+    info->used_bytes = D.total;
+    return CCD_OK;
 }
 
 ccd_status ccd_err_from_bounds(int kind, const double *verts, int64_t n, int ms_nonzero,
@@ -2192,7 +2572,9 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int3
         (int64_t)h.tq_deep, (int64_t)h.a_tasks_deep, (int64_t)h.split_chunks_deep,
         (int64_t)h.evals_shared_deep, h.mid, (int64_t)h.checks_pool, (int64_t)h.evals_pool,
         (int64_t)h.tq_deep_ee, (int64_t)h.a_tasks_deep_ee, (int64_t)h.evals_pool_ee,
-        (int64_t)h.tq_small_ee, (int64_t)h.evals_small_ee};
+        (int64_t)h.tq_small_ee, (int64_t)h.evals_small_ee, h.jumbo, h.pages_peak,
+        (int64_t)h.tq_pool, (int64_t)h.tq_pool_ee, (int64_t)h.pool_iters,
+        (int64_t)h.pool_serial};
     for (int i = 0; i < count && i < CCD_NUM_COUNTERS; ++i) counters[i] = all[i];
     return CCD_OK;
 }
@@ -2221,6 +2603,8 @@ const char *ccd_status_str(int status)
     case CCD_ERR_TIMEOUT: return "bounded device wait gave up";
     case CCD_ERR_CUDA: return "CUDA launch or copy failed";
     case CCD_ERR_CAPACITY: return "frontier exceeded its slot; conservative fallback used";
+    case CCD_ERR_BUSY: return "no room for the request now, or it already runs";
+    case CCD_ERR_CANCELLED: return "request cancelled";
     default: return "unknown status";
     }
 }
@@ -2283,6 +2667,7 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
     off = align256(off + sizeof(int) * (size_t)n);          // overflow
     off = align256(off + (size_t)n);                        // overflow levels
     off = align256(off + sizeof(int) * (size_t)n);          // deep list
+    off = align256(off + sizeof(int) * (size_t)n);          // deferred (full-size) list
     off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
     off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
                              (size_t)(sms * POOL_BLOCKS_PER_SM));   // pooled-solver slots
@@ -2292,60 +2677,53 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
     return off;
 }
 
-template <int DT>
-ccd_status launch_multi_solvers(const Params &p, const ccd_segment *segs, int nseg, char *ws,
-                                Box *pool_mem, PoolMeta *pool_meta, int sms, int pool_cap,
-                                size_t off_small,
-                                int nb_small,
-                                long long cap_small, size_t off_deep, int nb_deep,
-                                long long cap_deep, cudaStream_t st)
-{
-    const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
-    const size_t tq_deep = sizeof(SharedUV);
-    if (cudaFuncSetAttribute(solve_kernel_seg<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tq_deep) != cudaSuccess)
-        return CCD_ERR_CUDA;
-    // pooled stage: one launch per kind over the survivor list
-    pool_kernel<CCD_KIND_VF><<<pool_blocks(pool_kernel<CCD_KIND_VF>, sms), 32, 0, st>>>(
-        p, pool_mem, pool_meta, pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool, segs, nseg);
-    pool_kernel<CCD_KIND_EE><<<pool_blocks(pool_kernel<CCD_KIND_EE>, sms), 32, 0, st>>>(
-        p, pool_mem, pool_meta, pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool_ee, segs,
-        nseg);
-    stage_mark(2, st);
-    solve_kernel_seg<SMALL_THREADS><<<nb_small, SMALL_THREADS, tq_small, st>>>(
-        p, segs, nseg, 0, (Box *)(ws + off_small), cap_small);
-    order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &p.hdr->overflow, p.deep_list);
-    stage_mark(3, st);
-    solve_kernel_seg<DT><<<nb_deep, DT, tq_deep, st>>>(p, segs, nseg, 1, (Box *)(ws + off_deep),
-                                                       cap_deep);
-    stage_mark(4, st);
-    return CCD_OK;
-}
+// One segmented batch, laid out in its workspace.  The deep tier's pages are
+// the workspace's own, or (served batches) a pool shared with other batches,
+// in which case the workspace holds only the full-size slots.
+struct MultiPlan {
+    Params p;
+    Tuned T;
+    int sms;
+    const ccd_segment *segs;
+    int nseg;
+    long long bound;
+    char *ws;
+    Box *pool_mem;
+    PoolMeta *pool_meta;
+    size_t off_small;
+    int nb_small;
+    DeepLayout D;
+    PagePool pages;
+};
 
-ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
-                     int64_t max_itr_bound, uint8_t *collides, double *toi, double *out_tol,
-                     int64_t *checks, const ccd_tuning *tuning, void *workspace, size_t ws_bytes,
-                     void *stream)
+ccd_status multi_plan(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
+                      int64_t max_itr_bound, uint8_t *collides, double *toi, double *out_tol,
+                      int64_t *checks, const ccd_tuning *tuning, void *workspace,
+                      size_t ws_bytes, const PagePool *shared, MultiPlan *M)
 {
     if (n < 0 || n >= 0x7fffffffLL || max_itr_bound <= 0 || nseg < 0) return CCD_ERR_ARG;
     if (n > 0 && (!verts || !segs || nseg < 1 || !collides || !toi || !out_tol)) return CCD_ERR_ARG;
     if (!workspace) return CCD_ERR_WORKSPACE;
     const int sms = device_sms();
     if (sms <= 0) return CCD_ERR_CUDA;
-    Tuned T;
-    if (!resolve_tuning(tuning, sms, &T)) return CCD_ERR_ARG;
-    const size_t fixed = multi_fixed_bytes(n, sms, T);
-    const size_t per = sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound);
-    if (ws_bytes < fixed + per) return CCD_ERR_WORKSPACE;
-    long long nb_deep = (long long)((ws_bytes - fixed) / per);
-    if (nb_deep > T.deep_slots) nb_deep = T.deep_slots;
-
-    cudaStream_t st = (cudaStream_t)stream;
+    MultiPlan m{};
+    if (!resolve_tuning(tuning, sms, &m.T)) return CCD_ERR_ARG;
+    const size_t fixed = multi_fixed_bytes(n, sms, m.T);
+    if (shared) {
+        const size_t slots = JUMBO_SLOTS * align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound));
+        if (ws_bytes < fixed + slots) return CCD_ERR_WORKSPACE;
+        m.D.paged = true;
+        m.D.nb_deep = m.T.deep_slots;
+        m.D.nb_jumbo = JUMBO_SLOTS;
+        m.D.cap_deep = deep_cap(max_itr_bound);
+        m.D.off_slots = fixed;
+        m.D.total = fixed + slots;
+    } else if (!deep_layout(fixed, ws_bytes, max_itr_bound, m.T.deep_slots, &m.D) ||
+               m.D.cap_deep < deep_cap(max_itr_bound)) {
+        return CCD_ERR_WORKSPACE;
+    }
     char *ws = (char *)workspace;
-    if (cudaMemsetAsync(ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
-    if (n == 0) return CCD_OK;
-
-    Params p;
+    Params &p = m.p;
     p.verts = verts; p.n = n; p.err = nullptr; p.err_stride = 0;
     p.ms = 0.0; p.delta = 0.0; p.max_itr = 0;
     p.collides = collides; p.toi = toi; p.out_tol = out_tol; p.checks = (long long *)checks;
@@ -2356,36 +2734,209 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.over_level = (unsigned char *)(ws + off); off = align256(off + (size_t)n);
     p.deep_list = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.jumbo = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
-    Box *pool_mem = (Box *)(ws + off);
-    off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
+    m.pool_mem = (Box *)(ws + off);
+    off = align256(off + sizeof(Box) * 3 * (size_t)m.T.pool_cap * POOL_SLOTS *
                              (size_t)(sms * POOL_BLOCKS_PER_SM));
-    PoolMeta *pool_meta = (PoolMeta *)(ws + off);
+    m.pool_meta = (PoolMeta *)(ws + off);
     off = align256(off + sizeof(PoolMeta) * POOL_SLOTS * (size_t)(sms * POOL_BLOCKS_PER_SM));
-    const size_t off_small = off;
-    const int nb_small = sms * T.small_blocks_per_sm;
+    m.off_small = off;
+    m.nb_small = sms * m.T.small_blocks_per_sm;
+    m.sms = sms;
+    m.segs = segs;
+    m.nseg = nseg;
+    m.bound = max_itr_bound;
+    m.ws = ws;
+    m.pages = shared ? *shared : make_pool(ws, m.D, p.hdr);
+    *M = m;
+    return CCD_OK;
+}
 
-    seg_validate_kernel<<<(nseg + 255) / 256, 256, 0, st>>>(segs, nseg, n, max_itr_bound, p.hdr);
-    stage_mark(0, st);
-    root_kernel_seg<<<(unsigned)((n + ROOT_THREADS - 1) / ROOT_THREADS), ROOT_THREADS, 0, st>>>(
-        p, segs, nseg);
-    stage_mark(1, st);
-    ccd_status r = T.deep_threads == 256
-                       ? launch_multi_solvers<256>(p, segs, nseg, ws, pool_mem, pool_meta,
-                                                   sms, T.pool_cap,
-                                                   off_small, nb_small,
-                                                   T.small_cap, fixed, (int)nb_deep,
-                                                   deep_cap(max_itr_bound), st)
-                       : launch_multi_solvers<512>(p, segs, nseg, ws, pool_mem, pool_meta,
-                                                   sms, T.pool_cap,
-                                                   off_small, nb_small,
-                                                   T.small_cap, fixed, (int)nb_deep,
-                                                   deep_cap(max_itr_bound), st);
+template <int DT>
+ccd_status set_deep_attributes()
+{
+    const size_t tq_deep = sizeof(SharedUV);
+    for (auto *k : {solve_kernel_seg<DT, true>, solve_kernel_seg<DT, false>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
+            cudaSuccess)
+            return CCD_ERR_CUDA;
+    return CCD_OK;
+}
+
+// Header reset, segment validation, level 0, the pooled and one-warp
+// stages, and the deep list in schedule order.
+ccd_status multi_front(const MultiPlan &M, bool init_pool, cudaStream_t st)
+{
+    const Params &p = M.p;
+    if (cudaMemsetAsync(M.ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
+    if (p.n == 0) return CCD_OK;
+    ccd_status r = M.T.deep_threads == 256 ? set_deep_attributes<256>() : set_deep_attributes<512>();
     if (r != CCD_OK) return r;
+    seg_validate_kernel<<<(M.nseg + 255) / 256, 256, 0, st>>>(M.segs, M.nseg, p.n, M.bound, p.hdr);
+    stage_mark(0, st);
+    if (init_pool && M.D.paged)
+        pool_init_kernel<<<(M.D.nwords + 255) / 256, 256, 0, st>>>(M.pages.bits, M.D.nwords,
+                                                                   (int)M.D.npages);
+    root_kernel_seg<<<(unsigned)((p.n + ROOT_THREADS - 1) / ROOT_THREADS), ROOT_THREADS, 0, st>>>(
+        p, M.segs, M.nseg);
+    stage_mark(1, st);
+    const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
+    // pooled stage: one launch per kind over the survivor list
+    pool_kernel<CCD_KIND_VF><<<pool_blocks(pool_kernel<CCD_KIND_VF>, M.sms), 32, 0, st>>>(
+        p, M.pool_mem, M.pool_meta, M.T.pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool,
+        M.segs, M.nseg);
+    pool_kernel<CCD_KIND_EE><<<pool_blocks(pool_kernel<CCD_KIND_EE>, M.sms), 32, 0, st>>>(
+        p, M.pool_mem, M.pool_meta, M.T.pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool_ee,
+        M.segs, M.nseg);
+    stage_mark(2, st);
+    solve_kernel_seg<SMALL_THREADS, false><<<M.nb_small, SMALL_THREADS, tq_small, st>>>(
+        p, M.segs, M.nseg, 0, (Box *)(M.ws + M.off_small), M.T.small_cap, PagePool{});
+    order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &p.hdr->overflow, p.deep_list);
+    stage_mark(3, st);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
 
+// The deep stage (paged), one round of at most slice_ns (0: until the list
+// is empty); or, for a contiguous layout, the whole deep stage.
+template <int DT>
+void multi_deep_launch(const MultiPlan &M, long long slice_ns, cudaStream_t st)
+{
+    const size_t tq_deep = sizeof(SharedUV);
+    if (M.D.paged)
+        solve_kernel_seg<DT, true><<<M.D.nb_deep, DT, tq_deep, st>>>(
+            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns);
+    else
+        solve_kernel_seg<DT, false><<<M.D.nb_deep, DT, tq_deep, st>>>(
+            M.p, M.segs, M.nseg, 1, (Box *)(M.ws + M.D.off_slots), M.D.cap_deep, PagePool{});
+}
+
+ccd_status multi_deep(const MultiPlan &M, long long slice_ns, cudaStream_t st)
+{
+    if (M.p.n == 0) return CCD_OK;
+    if (slice_ns > 0 &&
+        cudaMemsetAsync(&M.p.hdr->round_start, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return CCD_ERR_CUDA;
+    if (M.T.deep_threads == 256) multi_deep_launch<256>(M, slice_ns, st);
+    else multi_deep_launch<512>(M, slice_ns, st);
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+// The queries the paged deep stage deferred, restarted in full-size slots.
+ccd_status multi_jumbo(const MultiPlan &M, cudaStream_t st)
+{
+    if (M.p.n > 0 && M.D.paged) {
+        const size_t tq_deep = sizeof(SharedUV);
+        Box *slots = (Box *)(M.ws + M.D.off_slots);
+        if (M.T.deep_threads == 256)
+            solve_kernel_seg<256, false><<<M.D.nb_jumbo, 256, tq_deep, st>>>(
+                M.p, M.segs, M.nseg, 2, slots, M.D.cap_deep, PagePool{});
+        else
+            solve_kernel_seg<512, false><<<M.D.nb_jumbo, 512, tq_deep, st>>>(
+                M.p, M.segs, M.nseg, 2, slots, M.D.cap_deep, PagePool{});
+    }
+    stage_mark(4, st);
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
+                     int64_t max_itr_bound, uint8_t *collides, double *toi, double *out_tol,
+                     int64_t *checks, const ccd_tuning *tuning, void *workspace, size_t ws_bytes,
+                     void *stream)
+{
+    MultiPlan M;
+    ccd_status r = multi_plan(verts, n, segs, nseg, max_itr_bound, collides, toi, out_tol, checks,
+                              tuning, workspace, ws_bytes, nullptr, &M);
+    if (r != CCD_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((r = multi_front(M, true, st)) != CCD_OK) return r;
+    if (n == 0) return CCD_OK;
+    if ((r = multi_deep(M, 0, st)) != CCD_OK) return r;
+    return multi_jumbo(M, st);
+}
+
 }  // namespace
+
+// ---- the served form's hooks (see internal.h) -------------------------------------
+
+namespace ccd_internal {
+
+namespace {
+PagePool to_pages(const FrontierPool &f)
+{
+    PagePool p{};
+    p.base = (Box *)f.pages;
+    p.bits = f.bits;
+    p.nwords = f.nwords;
+    p.used = f.counters;
+    p.peak = f.counters ? f.counters + 1 : nullptr;
+    return p;
+}
+
+ccd_status plan(const ServedBatch &b, const FrontierPool &pool, MultiPlan *M)
+{
+    const PagePool pages = to_pages(pool);
+    return multi_plan(b.verts, b.n, b.segs, b.nseg, b.max_itr_bound, b.collides, b.toi,
+                      b.out_tol, b.checks, nullptr, b.workspace, b.ws_bytes, &pages, M);
+}
+}  // namespace
+
+size_t page_bytes() { return PAGE_BYTES; }
+size_t pool_bytes(long long npages) { return ::pool_bytes(npages); }
+
+ccd_status pool_init(const FrontierPool &pool, cudaStream_t st)
+{
+    if (pool.npages < 1 || !pool.bits || !pool.pages) return CCD_ERR_ARG;
+    pool_init_kernel<<<(pool.nwords + 255) / 256, 256, 0, st>>>(pool.bits, pool.nwords,
+                                                                (int)pool.npages);
+    if (pool.counters && cudaMemsetAsync(pool.counters, 0, 2 * sizeof(int), st) != cudaSuccess)
+        return CCD_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
+}
+
+size_t served_workspace_bytes(int64_t n, int64_t max_itr_bound)
+{
+    if (n < 0 || n >= 0x7fffffffLL || max_itr_bound <= 0) return 0;
+    const int sms = device_sms();
+    Tuned T;
+    if (sms <= 0 || !resolve_tuning(nullptr, sms, &T)) return 0;
+    return multi_fixed_bytes(n, sms, T) +
+           JUMBO_SLOTS * align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound));
+}
+
+size_t header_bytes() { return sizeof(Header); }
+
+ccd_status served_front(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st)
+{
+    MultiPlan M;
+    ccd_status r = plan(b, pool, &M);
+    return r != CCD_OK ? r : multi_front(M, false, st);
+}
+
+ccd_status served_deep_round(const ServedBatch &b, const FrontierPool &pool, long long slice_ns,
+                             cudaStream_t st)
+{
+    MultiPlan M;
+    ccd_status r = plan(b, pool, &M);
+    return r != CCD_OK ? r : multi_deep(M, slice_ns, st);
+}
+
+ccd_status served_finish(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st)
+{
+    MultiPlan M;
+    ccd_status r = plan(b, pool, &M);
+    return r != CCD_OK ? r : multi_jumbo(M, st);
+}
+
+long long served_deep_left(const void *header)
+{
+    const Header *h = (const Header *)header;
+    return h->head_deep >= h->overflow ? 0 : (long long)(h->overflow - h->head_deep);
+}
+
+int served_status(const void *header) { return ((const Header *)header)->status; }
+
+}  // namespace ccd_internal
 
 extern "C" {
 
@@ -2396,8 +2947,7 @@ size_t ccd_multi_workspace_bytes(int64_t n, int64_t max_itr_bound, const ccd_tun
     if (sms <= 0) return 0;
     Tuned T;
     if (!resolve_tuning(tuning, sms, &T)) return 0;
-    return multi_fixed_bytes(n, sms, T) +
-           sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound) * (size_t)T.deep_slots;
+    return multi_fixed_bytes(n, sms, T) + default_deep_bytes(max_itr_bound, T.deep_slots);
 }
 
 ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
@@ -2711,6 +3261,7 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     p.over = (int *)(ws + STATIC_OFF_OVER);
     p.over_level = nullptr;   // no deep-tier ordering in the static-scratch path
     p.deep_list = nullptr;
+    p.jumbo = nullptr;
     p.kappa = (double *)(ws + STATIC_OFF_KAPPA);
     Header *h = p.hdr;
 
@@ -2723,10 +3274,10 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
         cudaSuccess)
         return CCD_ERR_CUDA;
     solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<STATIC_SMALL_BLOCKS, SMALL_THREADS, tq_small, st>>>(
-        p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP, p.surv, &h->survivors,
+        p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP, PagePool{}, p.surv, &h->survivors,
         &h->head_small, p.over, nullptr, &h->overflow);
     solve_kernel<CCD_KIND_VF, DEEP_THREADS><<<STATIC_DEEP_SLOTS, DEEP_THREADS, tq_deep, st>>>(
-        p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP, p.over, &h->overflow, &h->head_deep,
-        nullptr, nullptr, nullptr);
+        p, 1, (Box *)(ws + STATIC_OFF_DEEP), STATIC_DEEP_CAP, PagePool{}, p.over, &h->overflow,
+        &h->head_deep, nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }

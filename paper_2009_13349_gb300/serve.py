@@ -1,255 +1,133 @@
-"""Continuous-batching CCD request server.
+"""Driver of the served form (the C server behind ccd_batch_begin / submit /
+poll / cancel / end in include/ccd.h): requests in, finished requests out.
 
-Clients submit requests -- a set of queries of one kind with their own
-delta, ms and m_I, as when many simulations' line searches call CCD with
-per-step tolerances.  The server keeps several CUDA streams ("lanes").
-Whenever a lane is free it forms a batch from the requests waiting at that
-moment (FIFO, up to ``max_batch`` queries) admitted against a device-memory
-budget that covers every batch in flight (inputs, outputs and workspace),
-uploads them into one device array, and runs one multi-instance call (one
-segment per request: per-request eps from the request's own bounds, Sec. 6).
-Batches on different lanes overlap on the device; requests that arrive
-while others run join the next free lane.  Results are identical to solving
-each request alone (the solvers are deterministic and independent of how
-queries are batched).
-
-The scheduling logic (admission, budget accounting, completion) is plain
-host code driving an executor; ``GpuExecutor`` runs batches through the C
-ABI.  A request larger than what one batch may hold, or whose memory alone
-exceeds the budget, is rejected at submission.
+Admission against the device budget, the device-resident request queue,
+batch formation, lanes, time-sliced deep rounds and result delivery all run
+in the library; this module keeps each request's host arrays alive until the
+server reports it, and offers the measurement helpers of the benchmark
+(real-time arrival replay, one call per request, latency statistics).
 """
 from __future__ import annotations
 
-import collections
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
 VF, EE = 0, 1
-QUERY_BYTES = 24 * 8 + 1 + 8 + 8   # inputs + collides + toi + out_tol
 
 
 @dataclass
 class Request:
     id: int
     kind: int
-    aos: object            # host (n, 24) float64 array or tensor, one query per row
+    aos: np.ndarray            # host (n, 24) float64, one query per row
     delta: float = 1e-6
     ms: float = 0.0
     max_itr: int = 10**6
     arrival: float = 0.0
-    # filled by the server
+    # filled when the request finishes
     collides: np.ndarray = None
     toi: np.ndarray = None
     out_tol: np.ndarray = None
+    checks: np.ndarray = None
+    status: int = None
     done: float = None
-    batch: int = None
 
     @property
     def n(self) -> int:
         return int(self.aos.shape[0])
 
 
-class RejectedRequest(ValueError):
-    pass
-
-
-@dataclass
-class _Batch:
-    id: int
-    lane: int
-    requests: list
-    nbytes: int
-    handle: object = None
-
-
-def cost_class(r: Request) -> int:
-    """Requests whose minimum separation exceeds their tolerance subdivide a
-    whole |F| <= d region down to w(B) < delta (often to the check limit);
-    they are batched only with each other so that cheap requests do not wait
-    for them."""
-    return int(r.ms > 0.0 and r.delta < r.ms)
-
-
 class Server:
-    """Continuous batching over ``lanes`` executor lanes within ``budget`` bytes.
-    A batch takes requests from the FIFO head while they share the head's
-    cost class (``classify``; None puts every request in one class)."""
+    """One C server (see include/ccd.h, "The served form")."""
 
-    def __init__(self, executor, lanes: int = 4, budget: int = 40 << 30,
-                 max_batch: int = 1 << 20, clock=time.perf_counter, classify=cost_class):
-        self.ex = executor
-        self.lanes = lanes
-        self.budget = int(budget)
-        self.max_batch = int(max_batch)
+    def __init__(self, budget: int = 40 << 30, lanes: int = 4, max_batch: int = 1 << 20,
+                 max_itr_bound: int = 10**6, deep_slice_us: int = 20_000, clock=time.perf_counter,
+                 **config):
+        from . import ccd
+        self.native = ccd.NativeServer(budget_bytes=int(budget), lanes=int(lanes),
+                                       max_batch=int(max_batch), max_itr_bound=int(max_itr_bound),
+                                       deep_slice_us=int(deep_slice_us), **config)
         self.clock = clock
-        self.waiting = collections.deque()
-        self.busy = {}                  # lane -> _Batch
-        self.in_flight_bytes = 0
+        self.pending = {}          # ticket -> Request
         self.completed = []
-        self._next_batch = 0
-        self.peak_bytes = 0
-        self.classify = classify
 
-    def batch_bytes(self, n: int) -> int:
-        return int(n) * QUERY_BYTES + self.ex.workspace_bytes(int(n))
-
-    def submit(self, req: Request) -> None:
-        if req.n > self.max_batch or self.batch_bytes(req.n) > self.budget:
-            raise RejectedRequest(f"request {req.id}: {req.n} queries exceed the batch or "
-                                  f"memory budget")
+    def submit(self, req: Request) -> bool:
+        """Queues the request; False when the server has no room for it now."""
+        req.aos = np.ascontiguousarray(req.aos, dtype=np.float64)
+        req.collides = np.empty(req.n, dtype=np.uint8)
+        req.toi = np.empty(req.n, dtype=np.float64)
+        req.out_tol = np.empty(req.n, dtype=np.float64)
+        req.checks = np.empty(req.n, dtype=np.int64)
+        t = self.native.submit(req.kind, req.aos, req.ms, req.delta, req.max_itr, req.collides,
+                               req.toi, req.out_tol, req.checks)
+        if t is None:
+            return False
         if req.arrival == 0.0:
             req.arrival = self.clock()
-        self.waiting.append(req)
-
-    def _admit(self, lane: int) -> bool:
-        """Form one batch for a free lane from the FIFO head, within budget."""
-        take, n = [], 0
-        room = self.budget - self.in_flight_bytes
-        cls = self.classify(self.waiting[0]) if (self.classify and self.waiting) else None
-        while self.waiting:
-            r = self.waiting[0]
-            if n + r.n > self.max_batch or self.batch_bytes(n + r.n) > room:
-                break
-            if cls is not None and self.classify(r) != cls:
-                break
-            take.append(self.waiting.popleft())
-            n += r.n
-        if not take:
-            return False
-        b = _Batch(self._next_batch, lane, take, self.batch_bytes(n))
-        self._next_batch += 1
-        self.in_flight_bytes += b.nbytes
-        self.peak_bytes = max(self.peak_bytes, self.in_flight_bytes)
-        for r in take:
-            r.batch = b.id
-        b.handle = self.ex.launch(lane, take)
-        self.busy[lane] = b
+        self.pending[t] = req
         return True
 
-    def poll(self) -> list:
-        """Harvest finished batches, then give free lanes new work."""
-        done = []
-        for lane, b in list(self.busy.items()):
-            if self.ex.ready(b.handle):
-                now = self.clock()
-                self.ex.harvest(b.handle, b.requests)
-                for r in b.requests:
-                    r.done = now
-                done.extend(b.requests)
-                self.in_flight_bytes -= b.nbytes
-                del self.busy[lane]
-        for lane in range(self.lanes):
-            if lane not in self.busy and self.waiting:
-                if not self._admit(lane):
-                    break
-        self.completed.extend(done)
-        return done
+    def poll(self, wait_us: int = 0) -> list:
+        out = []
+        for t, status in self.native.poll(wait_us=wait_us):
+            r = self.pending.pop(t)
+            r.status = status
+            r.done = self.clock()
+            out.append(r)
+        self.completed.extend(out)
+        return out
+
+    def cancel(self, req_ticket: int) -> int:
+        return self.native.cancel(req_ticket)
 
     def idle(self) -> bool:
-        return not self.waiting and not self.busy
+        return not self.pending
 
-    def drain(self, sleep: float = 0.0) -> None:
-        while not self.idle():
-            self.poll()
-            if sleep:
-                time.sleep(sleep)
+    def drain(self, wait_us: int = 1000) -> None:
+        while self.pending:
+            self.poll(wait_us)
 
+    def stats(self) -> dict:
+        return self.native.stats()
 
-class GpuExecutor:
-    """Runs a batch of requests on one CUDA stream per lane through the C ABI:
-    per-request uploads into one (24, n) device array, per-segment eps from
-    bounds, ccd_multi_batch, and result copies into pinned host memory."""
-
-    def __init__(self, lanes: int, max_itr_bound: int = 10**6, tuning=None, device=None):
-        import torch
-        from . import ccd
-        self.torch, self.ccd = torch, ccd
-        self.dev = torch.device(device or "cuda")
-        self.streams = [torch.cuda.Stream(self.dev) for _ in range(lanes)]
-        self.max_itr_bound = int(max_itr_bound)
-        self.tuning = tuning
-
-    def workspace_bytes(self, n: int) -> int:
-        return self.ccd.multi_workspace_bytes(max(n, 1), self.max_itr_bound, self.tuning)
-
-    def launch(self, lane: int, reqs: list):
-        torch, ccd = self.torch, self.ccd
-        s = self.streams[lane]
-        n = sum(r.n for r in reqs)
-        seg = ccd.make_segments([r.n for r in reqs], [r.kind for r in reqs],
-                                [r.ms for r in reqs], [r.delta for r in reqs],
-                                [r.max_itr for r in reqs])
-        with torch.cuda.stream(s):
-            aos = torch.empty((n, 24), dtype=torch.float64, device=self.dev)
-            verts = torch.empty((24, n), dtype=torch.float64, device=self.dev)
-            off = 0
-            for r in reqs:
-                src = r.aos if isinstance(r.aos, torch.Tensor) else torch.from_numpy(r.aos)
-                aos[off:off + r.n].copy_(src, non_blocking=True)
-                off += r.n
-            ccd.aos_to_soa(aos, verts, 0, stream=s)
-            seg_host = torch.from_numpy(seg.view(np.uint8).copy()).pin_memory()
-            seg_dev = seg_host.to(self.dev, non_blocking=True)
-            ws = torch.empty(self.workspace_bytes(n), dtype=torch.uint8, device=self.dev)
-            ccd.segments_err_from_bounds(verts, seg_dev, stream=s)
-            res = ccd.multi_batch(verts, seg_dev, self.max_itr_bound, ws=ws, tuning=self.tuning,
-                                  with_checks=False, stream=s)
-            host = (torch.empty(n, dtype=torch.uint8).pin_memory(),
-                    torch.empty(n, dtype=torch.float64).pin_memory(),
-                    torch.empty(n, dtype=torch.float64).pin_memory())
-            host[0].copy_(res.collides, non_blocking=True)
-            host[1].copy_(res.toi, non_blocking=True)
-            host[2].copy_(res.out_tol, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        # keep device tensors alive until the stream is past them
-        return {"event": ev, "host": host, "keep": (aos, verts, seg_host, seg_dev, ws, res)}
-
-    def ready(self, handle) -> bool:
-        return handle["event"].query()
-
-    def harvest(self, handle, reqs: list) -> None:
-        handle["event"].synchronize()
-        col, toi, tol = (h.numpy() for h in handle["host"])
-        off = 0
-        for r in reqs:
-            r.collides = col[off:off + r.n].copy()
-            r.toi = toi[off:off + r.n].copy()
-            r.out_tol = tol[off:off + r.n].copy()
-            off += r.n
-        handle["keep"] = None
+    def close(self):
+        self.native.close()
 
 
 def run_stream(server: Server, requests: list, clock=time.perf_counter, t0=None):
-    """Replays ``requests`` (sorted by their ``arrival`` offsets in seconds)
-    in real time: each is submitted once its arrival time has passed.
-    Returns the wall time from the first arrival to the last completion."""
+    """Replays ``requests`` (``arrival`` = offset in seconds) in real time:
+    each is submitted once its arrival time has passed (and again after a
+    poll if the server had no room).  Returns the wall time from the first
+    arrival to the last completion."""
     t0 = clock() if t0 is None else t0
-    pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    pending = sorted(requests, key=lambda r: r.arrival)
     offsets = {r.id: r.arrival for r in pending}
-    while pending or not server.idle():
+    i = 0
+    while i < len(pending) or not server.idle():
         now = clock() - t0
-        while pending and offsets[pending[0].id] <= now:
-            r = pending.popleft()
+        while i < len(pending) and offsets[pending[i].id] <= now:
+            r = pending[i]
             r.arrival = t0 + offsets[r.id]
-            server.submit(r)
-        server.poll()
+            if not server.submit(r):
+                break
+            i += 1
+        server.poll(wait_us=200)
     return clock() - t0
 
 
-def serial_baseline(executor, requests: list, clock=time.perf_counter, t0=None):
-    """One call per request, in arrival order, each waiting for the previous
-    (the one-launch-per-request form).  Same real-time arrival replay."""
+def serial_baseline(run_one, requests: list, clock=time.perf_counter, t0=None):
+    """One call per request, in arrival order, each after the previous
+    finished (the one-launch-per-request form), under the same real-time
+    arrivals; run_one(request) fills the request's outputs."""
     t0 = clock() if t0 is None else t0
     for r in sorted(requests, key=lambda r: r.arrival):
         start = t0 + r.arrival
         while clock() < start:
-            pass
+            time.sleep(0.0002)
         r.arrival = start
-        h = executor.launch(0, [r])
-        executor.harvest(h, [r])
+        run_one(r)
         r.done = clock()
     return clock() - t0
 

@@ -7,9 +7,9 @@ grazing-tangent motions), run twice, with ms = 0 and ms = 1e-4 (Sec. 5.1),
 delta = 1e-6, m_I = 1e6.  Every one of the 200,000 GPU answers of a
 constructed contact (vertex-on-vertex and grazing: 40 % of the queries) must
 collide with toi <= t*.  The oracle checks a random sample of each kind and
-ms; it is slow on this workload (about 0.85 us per check per core, and a
-quarter to two thirds of the queries run to the 10^6-check limit), so the
-sample is 5,000 queries per kind at ms = 0 and 2,000 per kind at ms = 1e-4.
+ms, 5,000 queries per kind and ms.  All 200,000 would take it about six
+core-hours (a quarter to two thirds of the queries run to the 10^6-check
+limit), beyond what one test run can spend.
 
 Multi-instance: 64 simulation instances with log-uniform sizes summing to
 20,000,000 queries (seed 3), per-instance scale and eps, in one segmented
@@ -66,7 +66,7 @@ def _assert_truth(col, toi, truth, t_star, label):
     assert np.all(col[truth == 0] == 0), f"{label}: a certified separation reported"
 
 
-@pytest.mark.parametrize("ms,sample", [(0.0, 5000), (1e-4, 2000)])
+@pytest.mark.parametrize("ms,sample", [(0.0, 5000), (1e-4, 5000)])
 def test_degenerate_heavy_100k(ccd, ms, sample):
     wl = W.degenerate_heavy(n=100_000, seed=2)
     rng = np.random.default_rng(202 + int(ms > 0))

@@ -187,16 +187,18 @@ def test_determinism_and_workspace_reuse(ccd):
 
 
 def test_capacity_fallback_is_conservative(ccd):
-    """A workspace with one deep slot of 1024 boxes: queries whose frontier
-    needs more return as at the check limit, flagged CCD_ERR_CAPACITY, and
-    the answer stays conservative (never a missed collision, toi never
-    later than the oracle's)."""
+    """A workspace too small for a full-size slot: its deep tier is one
+    contiguous slot of 1024 boxes, so queries whose frontier needs more
+    return as at the check limit, flagged CCD_ERR_CAPACITY, and the answer
+    stays conservative (never a missed collision, toi never later than the
+    oracle's)."""
     b = W.degenerate_heavy(n=200, seed=21).batches[0]
     n, max_itr = b.n, 10**6
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
     full = ccd.workspace_bytes(n, max_itr)
-    deep = ccd.DEEP_SLOTS_PER_SM * sms * ccd.deep_slot_bytes(max_itr)
-    ws = torch.empty(full - deep + 2 * 1024 * 24, dtype=torch.uint8, device="cuda")
+    fixed = ccd.workspace_layout(n, max_itr, full)["fixed_bytes"]
+    ws = torch.empty(fixed + 2 * 1024 * 24, dtype=torch.uint8, device="cuda")
+    lay = ccd.workspace_layout(n, max_itr, ws.numel())
+    assert lay["paged"] == 0 and lay["slot_boxes"] == 1024
     g, e = gpu_run(ccd, b.kind, b.verts, ws=ws)
     st, fb = ccd.workspace_status(ws)
     assert st == -5 and fb > 0
@@ -204,6 +206,29 @@ def test_capacity_fallback_is_conservative(ccd):
     assert np.all(g[0] >= o[0])
     both = (g[0] == 1) & (o[0] == 1)
     assert np.all(g[1][both] <= o[1][both])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_frontier_pool_size_changes_nothing(ccd, kind):
+    """The deep tier's page pool at two pages: nearly every deep query finds
+    it empty and restarts in a full-size slot.  Outputs equal the oracle's
+    and those of a default workspace, with no capacity fallback."""
+    b = W.degenerate_heavy(n=400, seed=23).batches[kind]
+    full = ccd.workspace(b.n, 10**6)
+    lay = ccd.workspace_layout(b.n, 10**6, full.numel())
+    assert lay["paged"] == 1 and lay["full_slots"] == 2
+    tiny = ccd.workspace(b.n, 10**6, pages=2)
+    assert ccd.workspace_layout(b.n, 10**6, tiny.numel())["pages"] == 2
+    g_full, e = gpu_run(ccd, kind, b.verts, ws=full)
+    c_full = ccd.workspace_counters(full)
+    g_tiny, _ = gpu_run(ccd, kind, b.verts, ws=tiny)
+    c_tiny = ccd.workspace_counters(tiny)
+    assert c_full["status"] == 0 and c_tiny["status"] == 0
+    assert c_tiny["deferred_queries"] > 0 and c_tiny["pages_peak"] <= 2
+    assert c_full["pages_peak"] <= lay["pages"]
+    for x, y in zip(g_full, g_tiny):
+        assert np.array_equal(x, y)
+    assert_parity(g_tiny, oracle_run(kind, b.verts, e), f"two-page pool kind={kind}")
 
 
 def test_full_size_simulation_sampled(ccd):

@@ -1,12 +1,24 @@
-"""Served mode on the GPU: every request's answer is the same in the mix as
-when solved alone (and as from the single-batch entry points)."""
+"""The served form on the GPU (the C server: ccd_batch_begin / submit / poll /
+cancel / end), with requests shaped like the served workload: the uniform
+unit-cube generator, sizes log-uniform, per-request delta in {1e-4, 1e-6},
+ms in {0, 1e-4}, m_I = 1e6.
+
+Every request's answer must equal the oracle's (on a sample of its queries;
+eps from the request's own bounds, Sec. 6) and the answer of a call of its
+own, while several batches are in flight at once and the deep stage runs in
+time-sliced rounds.
+"""
+import os
+
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2009_13349_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 1
 
 
 def test_aos_to_soa_layout_kernel():
@@ -19,35 +31,97 @@ def test_aos_to_soa_layout_kernel():
     assert torch.count_nonzero(out[:, :123]) == 0 and torch.count_nonzero(out[:, 1123:]) == 0
 
 
-def test_each_result_same_alone_and_in_the_mix():
-    from paper_2009_13349_gb300 import ccd
-    from paper_2009_13349_gb300.serve import GpuExecutor, Request, Server
-    rng = np.random.default_rng(17)
+def _requests(count, lo, hi, seed):
+    from paper_2009_13349_gb300.serve import Request
+    rng = np.random.default_rng(seed)
     reqs = []
-    for i in range(24):
+    for i in range(count):
         kind = int(rng.integers(0, 2))
-        n = int(np.exp(rng.uniform(np.log(50), np.log(20_000))))
-        b = W.unit_cube(kind, n, seed=1000 + i) if i % 3 else W.simulation_mixed(
-            n=2 * n, seed=2000 + i).batches[kind]
-        reqs.append(Request(i, kind, np.ascontiguousarray(b.verts),
-                            delta=float(rng.choice([1e-4, 1e-6])),
-                            ms=float(rng.choice([0.0, 1e-4])),
-                            max_itr=int(rng.choice([1000, 10**6]))))
-    ex = GpuExecutor(lanes=3, max_itr_bound=10**6,
-                     tuning={"deep_threads": 512, "deep_slots": 16, "small_blocks_per_sm": 8,
-                             "small_cap": 1024})
-    srv = Server(ex, lanes=3, budget=12 << 30, max_batch=60_000)
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        b = W.unit_cube(kind, n, seed=seed * 1000 + i)
+        reqs.append(Request(i, kind, b.verts, delta=float(rng.choice([1e-4, 1e-6])),
+                            ms=float(rng.choice([0.0, 1e-4])), max_itr=10**6))
+    return reqs
+
+
+def test_served_requests_equal_oracle_and_their_own_calls():
+    from paper_2009_13349_gb300 import ccd
+    from paper_2009_13349_gb300.serve import Server
+    reqs = _requests(28, 100, 20_000, seed=51)
+    srv = Server(budget=12 << 30, lanes=4, max_batch=40_000, deep_slice_us=5_000)
     for r in reqs:
-        srv.submit(r)
+        assert srv.submit(r)
     srv.drain()
+    st = srv.stats()
+    srv.close()
     assert len(srv.completed) == len(reqs)
-    assert len({r.batch for r in reqs}) > 1          # several batches, some shared
-    assert any(sum(q.batch == r.batch for q in reqs) > 1 for r in reqs)
+    assert all(r.status == 0 for r in reqs)
+    assert st["batches"] > 1 and st["batches"] < len(reqs)      # requests shared batches
+    assert st["lanes_busy_peak"] >= 2                           # batches overlapped
+    assert st["deep_rounds"] > st["batches"]                    # deep stages were sliced
+    assert 0 < st["pages_peak"] <= st["pages"]
+    rng = np.random.default_rng(52)
     for r in reqs:
         v = ccd.to_soa(r.aos)
         e = ccd.err_from_bounds(r.kind, v, ms_nonzero=r.ms > 0)
         alone = ccd.batch(r.kind, v, e, ms=r.ms, delta=r.delta, max_itr=r.max_itr)
         torch.cuda.synchronize()
-        assert np.array_equal(r.collides, alone.collides.cpu().numpy())
-        assert np.array_equal(r.toi, alone.toi.cpu().numpy())
-        assert np.array_equal(r.out_tol, alone.out_tol.cpu().numpy())
+        got = (r.collides, r.toi, r.out_tol, r.checks)
+        ref = (alone.collides.cpu().numpy(), alone.toi.cpu().numpy(),
+               alone.out_tol.cpu().numpy(), alone.checks.cpu().numpy())
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y), f"request {r.id}: served differs from its own call"
+        eo = oracle.err_from_bounds(r.kind, r.aos, ms_nonzero=r.ms > 0)
+        assert np.array_equal(e.cpu().numpy(), eo)
+        idx = np.sort(rng.choice(r.n, min(r.n, 40), replace=False))
+        o = oracle.ccd_batch(r.kind, r.aos[idx], eo, ms=r.ms, delta=r.delta, max_itr=r.max_itr,
+                             nthreads=NT)
+        for x, y in zip(got, o):
+            assert np.array_equal(x[idx], y), f"request {r.id}: served differs from the oracle"
+
+
+def test_served_backpressure_cancel_and_refusals():
+    from paper_2009_13349_gb300 import ccd
+    from paper_2009_13349_gb300.serve import Request, Server
+    reqs = _requests(12, 200, 900, seed=61)
+    # an inbox of 1,000 records: most requests wait for room
+    srv = Server(budget=4 << 30, lanes=2, max_batch=1000, inbox_queries=1000,
+                 max_itr_bound=10**6)
+    taken, refused = [], 0
+    for r in reqs:
+        if srv.submit(r):
+            taken.append(r)
+        else:
+            refused += 1
+    assert refused > 0
+    # a request larger than a batch, or with m_I above the bound, can never run
+    big = Request(99, 0, np.zeros((1001, 24)))
+    with pytest.raises(ccd.CCDError):
+        srv.submit(big)
+    with pytest.raises(ccd.CCDError):
+        srv.submit(Request(98, 0, np.zeros((10, 24)), max_itr=10**7))
+    srv.drain()
+    # the rest go in as room frees up; cancel the last one while it waits
+    rest = [r for r in reqs if r not in taken]
+    tickets = {}
+    for r in rest:
+        while not srv.submit(r):
+            srv.poll(wait_us=1000)
+        tickets[r.id] = max(srv.pending)
+    last = rest[-1]
+    code = srv.cancel(tickets[last.id])
+    srv.drain()
+    srv.close()
+    done = {r.id: r for r in srv.completed}
+    if code == 0:
+        assert done[last.id].status == -7
+    else:
+        assert code == -6 and done[last.id].status == 0     # it was already running
+    for r in reqs:
+        if r.status != 0:
+            continue
+        eo = oracle.err_from_bounds(r.kind, r.aos, ms_nonzero=r.ms > 0)
+        o = oracle.ccd_batch(r.kind, r.aos, eo, ms=r.ms, delta=r.delta, max_itr=r.max_itr,
+                             nthreads=NT)
+        for x, y in zip((r.collides, r.toi, r.out_tol, r.checks), o):
+            assert np.array_equal(x, y), f"request {r.id}"

@@ -1,139 +1,155 @@
-"""Scheduler of the continuous-batching server, on the CPU with a fake
-executor: FIFO admission, batching of waiting requests, the memory budget
-over all batches in flight, lane concurrency, routing of results, and
-rejection of requests that can never fit."""
+"""Host-side scheduling of the request server (csrc/serve_queue.h), on the
+CPU: where a request goes in the inbox ring, which waiting requests form a
+lane's batch, and which finished requests give their space back.  A
+randomized run of the server's host flow (submissions, batches on lanes of
+both priorities, completions out of order, reports, releases) checks that
+live requests never overlap in the inbox, every batch is a contiguous run of
+waiting requests of one class within the limits, high-priority lanes take
+only cheap requests, and space comes back in inbox order."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
 import numpy as np
 import pytest
 
-from paper_2009_13349_gb300.serve import QUERY_BYTES, RejectedRequest, Request, Server
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WAITING, RUNNING, DONE, CANCELLED = range(4)
 
 
-class FakeClock:
-    def __init__(self):
-        self.t = 0.0
-
-    def __call__(self):
-        return self.t
-
-
-class FakeExecutor:
-    """Completes a batch `dur` fake seconds after launch; results encode
-    (request id, position) so routing can be checked."""
-
-    def __init__(self, clock, ws_per_query=100, dur=1.0):
-        self.clock, self.ws_per_query, self.dur = clock, ws_per_query, dur
-        self.launches = []
-
-    def workspace_bytes(self, n):
-        return 1000 + self.ws_per_query * n
-
-    def launch(self, lane, reqs):
-        h = {"lane": lane, "reqs": [r.id for r in reqs], "t_end": self.clock() + self.dur}
-        self.launches.append(h)
-        return h
-
-    def ready(self, h):
-        return self.clock() >= h["t_end"]
-
-    def harvest(self, h, reqs):
-        for r in reqs:
-            r.collides = np.full(r.n, r.id % 2, np.uint8)
-            r.toi = r.id + np.arange(r.n) / 1e6
-            r.out_tol = np.zeros(r.n)
+@pytest.fixture(scope="module")
+def Q():
+    tmp = tempfile.mkdtemp()
+    so = os.path.join(tmp, "serve_queue_harness.so")
+    subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-I",
+                    os.path.join(ROOT, "paper_2009_13349_gb300", "csrc"), "-o", so,
+                    os.path.join(ROOT, "tests", "serve_queue_harness.cpp")], check=True)
+    L = ctypes.CDLL(so)
+    pl, pi, pu = (ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                  ctypes.POINTER(ctypes.c_ubyte))
+    L.h_alloc.argtypes = [pl, pl, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong]
+    L.h_alloc.restype = ctypes.c_longlong
+    L.h_select.argtypes = [pl, pl, pi, pi, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                           ctypes.c_int, pl, pl]
+    L.h_select.restype = ctypes.c_int
+    L.h_releasable.argtypes = [pi, pu, ctypes.c_int]
+    L.h_releasable.restype = ctypes.c_longlong
+    return L
 
 
-def req(i, n, kind=0, ms=0.0, delta=1e-6):
-    return Request(i, kind, np.zeros((n, 24)), ms=ms, delta=delta)
+def _arr(x, t):
+    return (t * max(1, len(x)))(*x)
 
 
-def test_fifo_batching_and_routing():
-    clk = FakeClock()
-    ex = FakeExecutor(clk)
-    s = Server(ex, lanes=2, budget=10**9, max_batch=100, clock=clk)
-    for i, n in enumerate([30, 30, 30, 30, 80, 20]):
-        s.submit(req(i, n))
-    s.poll()
-    # lane 0 takes the first three (90 <= 100; +30 would exceed), lane 1 the
-    # next one (30 + 80 > 100 stops there); the rest waits for a free lane
-    assert [h["reqs"] for h in ex.launches] == [[0, 1, 2], [3]]
-    clk.t = 1.0
-    done = s.poll()
-    assert sorted(r.id for r in done) == [0, 1, 2, 3]
-    assert [h["reqs"] for h in ex.launches][-1] == [4, 5]
-    clk.t = 2.0
-    s.poll()
-    assert s.idle() and len(s.completed) == 6
-    for r in s.completed:
-        assert r.toi[0] == r.id and r.collides[0] == r.id % 2
+def alloc(Q, reqs, cap, want):
+    return Q.h_alloc(_arr([r["off"] for r in reqs], ctypes.c_longlong),
+                     _arr([r["n"] for r in reqs], ctypes.c_longlong), len(reqs), cap, want)
 
 
-def test_budget_caps_memory_in_flight():
-    clk = FakeClock()
-    ex = FakeExecutor(clk, ws_per_query=10)
-    per = lambda n: n * QUERY_BYTES + 1000 + 10 * n
-    budget = per(40) + per(40) // 2          # room for one 40-query batch, not two
-    s = Server(ex, lanes=4, budget=budget, max_batch=40, clock=clk)
-    for i in range(6):
-        s.submit(req(i, 40))
-    steps = 0
-    while not s.idle():
-        s.poll()
-        assert s.in_flight_bytes <= budget
-        assert len(s.busy) <= 1
-        clk.t += 0.5
-        steps += 1
-        assert steps < 100
-    assert len(s.completed) == 6 and s.peak_bytes <= budget
+def select(Q, reqs, high, max_batch, max_segs):
+    f, k = ctypes.c_longlong(), ctypes.c_longlong()
+    ok = Q.h_select(_arr([r["off"] for r in reqs], ctypes.c_longlong),
+                    _arr([r["n"] for r in reqs], ctypes.c_longlong),
+                    _arr([r["state"] for r in reqs], ctypes.c_int),
+                    _arr([r["cls"] for r in reqs], ctypes.c_int), len(reqs), int(high), max_batch,
+                    max_segs, ctypes.byref(f), ctypes.byref(k))
+    return (f.value, k.value) if ok else None
 
 
-def test_lanes_bound_concurrency_and_late_arrivals_join():
-    clk = FakeClock()
-    ex = FakeExecutor(clk, dur=2.0)
-    s = Server(ex, lanes=3, budget=10**12, max_batch=10, clock=clk)
-    for i in range(5):
-        s.submit(req(i, 10))
-    s.poll()
-    assert len(s.busy) == 3
-    clk.t = 1.0
-    s.submit(req(5, 5))
-    s.submit(req(6, 5))
-    s.poll()
-    assert len(s.busy) == 3            # still running; newcomers wait
-    clk.t = 2.0
-    s.poll()                           # first three done; waiting ones admitted together
-    assert [h["reqs"] for h in ex.launches[3:]] == [[3], [4], [5, 6]]
-    clk.t = 4.0
-    s.poll()
-    assert s.idle() and len(s.completed) == 7
+def releasable(Q, reqs):
+    return Q.h_releasable(_arr([r["state"] for r in reqs], ctypes.c_int),
+                          _arr([int(r["reported"]) for r in reqs], ctypes.c_ubyte), len(reqs))
 
 
-def test_oversized_requests_are_rejected():
-    clk = FakeClock()
-    ex = FakeExecutor(clk)
-    s = Server(ex, lanes=1, budget=10**6, max_batch=50, clock=clk)
-    with pytest.raises(RejectedRequest):
-        s.submit(req(0, 51))
-    with pytest.raises(RejectedRequest):
-        s.submit(req(1, 49 * 100))     # within max_batch? no: also over budget
-    s2 = Server(ex, lanes=1, budget=2000, max_batch=10**6, clock=clk)
-    with pytest.raises(RejectedRequest):
-        s2.submit(req(2, 10))
+def test_inbox_ring_cases(Q):
+    cap = 100
+    assert alloc(Q, [], cap, 100) == 0 and alloc(Q, [], cap, 101) == -1
+    a = [{"off": 10, "n": 30}]
+    assert alloc(Q, a, cap, 60) == 40          # after the last one
+    assert alloc(Q, a, cap, 61) == -1          # neither after it nor before the first
+    assert alloc(Q, a, cap, 10) == 40
+    b = [{"off": 40, "n": 50}]
+    assert alloc(Q, b, cap, 20) == 0           # wraps to the start, before the first
+    assert alloc(Q, b, cap, 41) == -1
+    w = [{"off": 40, "n": 50}, {"off": 0, "n": 20}]   # wrapped
+    assert alloc(Q, w, cap, 20) == 20 and alloc(Q, w, cap, 21) == -1
 
 
-def test_batches_keep_cost_classes_apart():
-    clk = FakeClock()
-    ex = FakeExecutor(clk)
-    s = Server(ex, lanes=3, budget=10**12, max_batch=1000, clock=clk)
-    s.submit(req(0, 10))
-    s.submit(req(1, 10))
-    s.submit(req(2, 10, ms=1e-4, delta=1e-6))     # separation above tolerance
-    s.submit(req(3, 10, ms=1e-4, delta=1e-6))
-    s.submit(req(4, 10, ms=1e-4, delta=1e-3))     # separation below tolerance: cheap
-    s.poll()
-    assert [h["reqs"] for h in ex.launches] == [[0, 1], [2, 3], [4]]
-    s2 = Server(FakeExecutor(clk), lanes=1, budget=10**12, max_batch=1000, clock=clk,
-                classify=None)
-    for i in range(5):
-        s2.submit(req(i, 10, ms=1e-4 * (i % 2)))
-    s2.poll()
-    assert [h["reqs"] for h in s2.ex.launches] == [[0, 1, 2, 3, 4]]
+def test_batch_selection_cases(Q):
+    R = lambda off, n, st, c: {"off": off, "n": n, "state": st, "cls": c}
+    reqs = [R(0, 10, DONE, 0), R(10, 10, RUNNING, 0), R(20, 10, WAITING, 1),
+            R(30, 10, WAITING, 1), R(40, 10, WAITING, 0), R(50, 10, WAITING, 0)]
+    assert select(Q, reqs, False, 1000, 100) == (2, 2)    # oldest waiting run, one class
+    assert select(Q, reqs, True, 1000, 100) == (4, 2)     # a high lane skips class 1
+    assert select(Q, reqs, False, 15, 100) == (2, 1)      # the batch limit
+    assert select(Q, reqs, True, 1000, 1) == (4, 1)       # the request limit
+    wrap = [R(90, 10, WAITING, 0), R(0, 10, WAITING, 0)]
+    assert select(Q, wrap, False, 1000, 100) == (0, 1)    # not contiguous across the ring end
+    assert select(Q, [R(0, 5, RUNNING, 0)], False, 10, 10) is None
+
+
+def test_release_in_order(Q):
+    reqs = [{"state": DONE, "reported": True}, {"state": CANCELLED, "reported": True},
+            {"state": DONE, "reported": False}, {"state": DONE, "reported": True}]
+    assert releasable(Q, reqs) == 2
+    reqs[2]["reported"] = True
+    assert releasable(Q, reqs) == 4
+    assert releasable(Q, [{"state": RUNNING, "reported": False}] + reqs) == 0
+
+
+def test_randomized_host_flow(Q):
+    rng = np.random.default_rng(5)
+    cap, max_batch, max_segs = 5000, 1200, 6
+    lanes = [{"high": i < 2, "batch": None} for i in range(4)]
+    order, live_done = [], 0
+    next_id = 0
+    for step in range(3000):
+        op = rng.random()
+        if op < 0.45:                                       # a submission
+            n = int(rng.integers(1, 900))
+            off = alloc(Q, order, cap, n)
+            if off >= 0:
+                new = {"id": next_id, "off": off, "n": n, "state": WAITING,
+                       "cls": int(rng.random() < 0.3), "reported": False}
+                # never overlaps a live request
+                for r in order:
+                    assert off + n <= r["off"] or r["off"] + r["n"] <= off
+                order.append(new)
+                next_id += 1
+        elif op < 0.75:                                     # an idle lane takes a batch
+            L = lanes[int(rng.integers(0, 4))]
+            if L["batch"] is None:
+                got = select(Q, order, L["high"], max_batch, max_segs)
+                if got is not None:
+                    f, k = got
+                    run = order[f:f + k]
+                    assert 1 <= k <= max_segs and sum(r["n"] for r in run) <= max_batch
+                    assert all(r["state"] == WAITING for r in run)
+                    assert len({r["cls"] for r in run}) == 1
+                    if L["high"]:
+                        assert run[0]["cls"] == 0
+                    first_wait = [r for r in order if r["state"] == WAITING and
+                                  (not L["high"] or r["cls"] == 0)][0]
+                    assert run[0] is first_wait
+                    for a, b in zip(run, run[1:]):
+                        assert b["off"] == a["off"] + a["n"]
+                    for r in run:
+                        r["state"] = RUNNING
+                    L["batch"] = run
+        elif op < 0.9:                                      # a lane's batch finishes
+            busy = [L for L in lanes if L["batch"] is not None]
+            if busy:
+                L = busy[int(rng.integers(0, len(busy)))]
+                for r in L["batch"]:
+                    r["state"] = DONE
+                L["batch"] = None
+        else:                                               # reports, then releases
+            for r in order:
+                if r["state"] in (DONE, CANCELLED):
+                    r["reported"] = True
+            k = releasable(Q, order)
+            assert all(r["state"] in (DONE, CANCELLED) for r in order[:k])
+            live_done += k
+            order = order[k:]
+    assert live_done > 100 and next_id > 500
