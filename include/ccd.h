@@ -437,14 +437,13 @@ ccd_status ccd_aos_to_soa(const double *aos, int64_t n, double *soa, int64_t ld,
  * Vertex-face batch that allocates nothing (the paper has no counterpart;
  * this is a deployment variant of ccd_vf_batch).
  *
- * For callers that cannot allocate device memory: code running while a CUDA
- * graph is captured on its stream, real-time loops that must not enter the
- * allocator, plugins inside a host application that owns every allocation,
- * processes under a fixed device-memory quota.  Instead of a caller
- * workspace it uses a 40 MiB file-scope device array that every GPU loading
- * this library holds until the process exits.  Inputs and outputs are as for
- * ccd_vf_batch and still come from the caller; results are identical to
- * ccd_vf_batch's for the same arguments.
+ * For callers that cannot allocate device memory: real-time loops that must
+ * not enter the allocator, plugins inside a host application that owns every
+ * allocation, processes under a fixed device-memory quota.  Instead of a
+ * caller workspace it uses a 40 MiB file-scope device array that every GPU
+ * loading this library holds until the process exits.  Inputs and outputs
+ * are as for ccd_vf_batch and still come from the caller; results are
+ * identical to ccd_vf_batch's for the same arguments.
  *
  * Limits: n <= 32768 queries and max_itr <= 65536 per call; larger requests
  * return CCD_ERR_WORKSPACE without doing any work.  The first call on each
@@ -475,18 +474,23 @@ ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const double *err
  *  - per lane (a CUDA stream) the region of one batch;
  *  - a pool of deep-frontier pages shared by every lane's deep stage.
  * Whenever a lane is free, poll() and submit() give it the oldest run of
- * waiting requests of one cost class (requests with ms > delta subdivide
- * whole |F| <= ms regions and are batched apart; half of the lanes, at the
- * higher stream priority, take only the other class), up to max_batch
- * queries and max_segments requests.  On the lane's stream the batch's
- * segment table is gathered from the descriptors and its records turned into
- * planes, on the device; eps comes from each request's own bounds (Eq.
- * ccd-error / msccd-error over its points, Sec. 6), and the solver stages of
- * ccd_multi_batch run, the deep stage in rounds of deep_slice_us: a round's
- * blocks take no new query after the slice, which lets other lanes' kernels
- * onto the SMs, and poll() starts the next round.  No kernel waits for
- * anything.  Every request's outputs equal those of ccd_vf_batch /
- * ccd_ee_batch on its queries alone with eps from its own bounds.
+ * waiting requests of one cost class, up to max_batch queries and
+ * max_segments requests.  Requests with ms > delta subdivide whole |F| <= ms
+ * regions (about 10^6 checks per colliding query at the paper's m_I) and are
+ * "expensive": they run only on the last lane, at the lower stream priority,
+ * one batch (of at most 65,536 queries) at a time in arrival order; the
+ * other lanes, at the higher priority, take only cheap requests.  On the
+ * lane's stream the batch's segment table is gathered from the descriptors
+ * and its records turned into planes, on the device; eps comes from each
+ * request's own bounds (Eq. ccd-error / msccd-error over its points, Sec.
+ * 6), and the solver stages of ccd_multi_batch run.  The deep stage runs in
+ * rounds: when a cheap batch starts while an expensive one is in its deep
+ * stage, the latter's blocks are asked (a flag in mapped host memory) to take
+ * no new query, which lets the cheap batch's kernels onto the SMs, and
+ * poll() starts the next round; with deep_slice_us > 0 rounds also end after
+ * that long.  No kernel waits for anything.  Every request's outputs equal
+ * those of ccd_vf_batch / ccd_ee_batch on its queries alone with eps from
+ * its own bounds.
  *
  * Requests whose queries do not fit the inbox or the descriptor ring right
  * now are refused with CCD_ERR_BUSY (submit again after a poll); requests
@@ -494,7 +498,7 @@ ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const double *err
  * and are refused with CCD_ERR_ARG.  A waiting request can be cancelled.
  * One host thread drives a server; it uses the device current at begin.
  * poll() advances the batches (the next deep round, result copies): call it
- * at least every deep_slice_us while requests are in flight.
+ * often while requests are in flight.
  */
 typedef struct ccd_server ccd_server;
 
@@ -507,7 +511,7 @@ typedef struct {
     int32_t max_segments;    /* requests per batch (default 1024)               */
     int32_t pad;
     int64_t max_itr_bound;   /* largest m_I a request may ask for (10^6)        */
-    int64_t deep_slice_us;   /* deep round length in microseconds (20,000)      */
+    int64_t deep_slice_us;   /* deep rounds also end after this long (0: no)    */
 } ccd_server_config;         /* zero fields take the defaults */
 
 typedef struct {
@@ -527,6 +531,7 @@ typedef struct {
 typedef struct {
     int64_t submitted, completed, cancelled, busy_rejections;
     int64_t batches, deep_rounds;
+    int64_t yields;              /* deep rounds asked to end for a cheap batch  */
     int64_t inbox_peak_queries;  /* the most inbox records held at once         */
     int64_t pages;               /* frontier pages in the shared pool           */
     int32_t pages_peak;          /* the most pages held at once                 */

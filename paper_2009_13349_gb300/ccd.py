@@ -559,6 +559,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("cancelled", ctypes.c_int64), ("busy_rejections", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("deep_rounds", ctypes.c_int64),
+                ("yields", ctypes.c_int64),
                 ("inbox_peak_queries", ctypes.c_int64), ("pages", ctypes.c_int64),
                 ("pages_peak", ctypes.c_int32), ("lanes_busy_peak", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_size_t)]

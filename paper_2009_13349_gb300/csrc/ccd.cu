@@ -1471,12 +1471,24 @@ struct PoolMeta {
     double kap[3];
 };
 
+// What a slot's lanes decided in one iteration, for the slot's owner lane.
+struct PoolAgg {
+    int outcome;                  // 0 continue, 1 answered, 2 handed over
+    int fh;                       // a colliding box in the iteration (0 / 1)
+    int runs;                     // t split: runs of equal t_L that start here
+    int cnt0, cntk;               // t split: colliding boxes of the first / last run
+    int hits;                     // colliding boxes
+    int children;                 // u / v split: children written
+    unsigned long long at_fh;     // t_L numerator of the first colliding box
+    unsigned long long at_k;      // ... of the last run
+    double w_fh;
+};
+
 template <int KIND>
 struct PoolShared {
     PoolSlot st[POOL_SLOTS];
-    Box box[32];
-    double w[32];
-    int hit[32], term[32], lane_slot[32], lane_off[32];
+    PoolAgg agg[POOL_SLOTS];
+    int seg_slot[32];             // slot of the segment of lanes starting at a lane
     // distinct t values of an iteration (at most 32 runs + 31 gaps + 1)
     double tq[64][TWidth<KIND>::W];
     unsigned long long tv_a[64];
@@ -1562,7 +1574,9 @@ __global__ void __launch_bounds__(32)
         const bool active = S.qi >= 0;
         if (!__any_sync(FULL, active) && __all_sync(FULL, drained)) break;
 
-        // 2. place the slots' next boxes in the lanes, rotating the priority
+        // 2. place the slots' next boxes in the lanes, rotating the priority:
+        // slot s takes lanes [E_s, E_s + take_s); a lane finds its slot from
+        // the mask of segment starts
         const int rem = active ? (int)min(S.size - S.pos, 32LL) : 0;
         const int rrem = __shfl_sync(FULL, rem, (lane + rot) & 31);
         int inc = rrem;
@@ -1574,12 +1588,23 @@ __global__ void __launch_bounds__(32)
         const int total = __shfl_sync(FULL, inc, 31);
         const int E = __shfl_sync(FULL, inc - rrem, (lane - rot) & 31);
         const int take = (active && E < 32) ? min(rem, 32 - E) : 0;
-        for (int j = 0; j < take; ++j) {
-            sh.lane_slot[E + j] = lane;
-            sh.lane_off[E + j] = j;
-        }
         rot = (rot + 1) & 31;
+        const unsigned starts = __reduce_or_sync(FULL, take > 0 ? (1u << E) : 0u);
+        if (take > 0) sh.seg_slot[E] = lane;
         __syncwarp();
+        const int nbox = min(total, 32);
+        const bool have = lane < nbox;
+        const unsigned below = 0xffffffffu >> (31 - lane);          // lanes <= this one
+        const int st0 = have ? 31 - __clz(starts & below) : lane;    // first lane of my segment
+        const unsigned later = starts & ~below;
+        const int en0 = have ? (later ? __ffs(later) - 1 : nbox) : lane + 1;
+        const unsigned segmask = have ? ((en0 == 32 ? 0xffffffffu : ((1u << en0) - 1u)) &
+                                         ~((1u << st0) - 1u))
+                                      : 0u;
+        const int so = have ? sh.seg_slot[st0] : 0;
+        const int off = lane - st0;
+        iters += 1;
+        serial += (unsigned long long)__reduce_max_sync(FULL, (unsigned)take);
 
         // 3. one box per lane.  A slot's boxes sit in consecutive lanes in Q
         // order (ascending t_L), so the iteration's distinct t values get
@@ -1587,19 +1612,12 @@ __global__ void __launch_bounds__(32)
         // that id + 1; a slot change counts as a gap); their t-quantities are
         // computed once, one task per (t value, axis), then every lane takes
         // the corners of its box from them.
-        const int nbox = min(total, 32);
-        const bool have = lane < nbox;
-        iters += 1;
-        serial += (unsigned long long)__reduce_max_sync(FULL, (unsigned)take);
         BoxTest bt{false, false, 0.0};
         Box b = Box{{0ull, 0ull, 0ull}};
-        int so = 0;
+        Box *const sbase = mem + ((size_t)blockIdx.x * POOL_SLOTS + so) * 3 * (size_t)cap;
+        const PoolSlot &T = sh.st[so];
         if (have) {
-            so = sh.lane_slot[lane];
-            const PoolSlot &T = sh.st[so];
-            const Box *cur = mem + ((size_t)blockIdx.x * POOL_SLOTS + so) * 3 * (size_t)cap +
-                             (T.buf ? cap : 0);
-            b = cur[T.pos + sh.lane_off[lane]];
+            b = sbase[(T.buf ? cap : 0) + T.pos + off];
             evals += 1;
         }
         const unsigned long long at = b.a[0];
@@ -1631,7 +1649,6 @@ __global__ void __launch_bounds__(32)
         }
         __syncwarp();
         if (have) {
-            const PoolSlot &T = sh.st[so];
             long long km[3], kM[3];
             corners_keys<KIND>(sh.tq[tl], sh.tq[tl + 1], dyadic(b.a[1], T.k[1]),
                                dyadic(b.a[1] + 1, T.k[1]), dyadic(b.a[2], T.k[2]),
@@ -1640,80 +1657,149 @@ __global__ void __launch_bounds__(32)
             make_thresholds(meta[so].qp.eps, meta[so].qp.delta, TH);
             box_test_keys(km, kM, TH, meta[so].qp.ms, bt.hit, bt.term, bt.w);
         }
-        sh.box[lane] = b;
-        sh.hit[lane] = bt.hit;
-        sh.term[lane] = bt.term;
-        sh.w[lane] = bt.w;
-        __syncwarp();
 
-        // 4. the owner lane applies Algorithm 2 to its boxes, in Q order
-        if (take > 0) {
-            const QP &qq = meta[lane].qp;
-            Box *cur = mine + (S.buf ? cap : 0);
-            Box *nxt = mine + (S.buf ? 0 : cap);
-            Box *pend = mine + 2 * (size_t)cap;
-            (void)cur;
-            int outcome = 0;   // 0 continue, 1 answered, 2 hand over
-            long long n = 0;
-            for (int L = E; L < E + take; ++L) {
-                n = S.n_before + S.pos + (L - E) + 1;
-                if (!sh.hit[L]) continue;
-                const Box bb = sh.box[L];
-                if (!S.found) {
-                    S.found = 1;
-                    S.if_at = bb.a[0];
-                    S.first_w = sh.w[L];
-                    if (n >= qq.max_itr || sh.term[L] || !S.can_split) {
-                        write_result(p, S.qi, 1, dmul(qq.t_max, dyadic(S.if_at, S.k[0])),
-                                     sh.w[L], n);
-                        outcome = 1;
-                        break;
-                    }
-                } else if (n >= qq.max_itr) {
-                    write_result(p, S.qi, 1, dmul(qq.t_max, dyadic(S.if_at, S.k[0])), sh.w[L], n);
-                    outcome = 1;
-                    break;
+        // 4. Algorithm 2's bookkeeping for every slot at once, with the
+        // results of the sequential loop over the slot's boxes in Q order.
+        // Box at lane L is check n = n_before + pos + (L - E) + 1.  Ballots
+        // over the slot's lanes give its first colliding box fh, the first
+        // box that returns (A: n >= m_I, or the level's first colliding box
+        // terminating or unsplittable) and the first whose children would
+        // not fit (O); the query returns at A if A <= O, is handed on at O
+        // otherwise, else every colliding box writes its children where the
+        // loop would: u / v splits at the slot's count plus a segmented
+        // prefix count; t splits in runs of equal t_L, all left children of
+        // a run, then its right children, where a run still open at the end
+        // of the iteration keeps its right children in the pending list.
+        const long long n_L = T.n_before + T.pos + off + 1;
+        const bool hit = have && bt.hit;
+        const unsigned Hs = __ballot_sync(FULL, hit) & segmask;
+        const int fh = Hs ? __ffs(Hs) - 1 : -1;
+        const int sd = T.sd;
+        const bool ans = hit && (n_L >= meta[so].qp.max_itr ||
+                                 (lane == fh && !T.found && (bt.term || !T.can_split)));
+        bool keep_r = true;
+        if (KIND == CCD_KIND_VF && hit && sd != 0) {   // right child meets the prism iff u_L + v_L <= 1
+            const int ku = T.k[1] + (sd == 1), kv = T.k[2] + (sd == 2);
+            const unsigned long long au = sd == 1 ? 2 * b.a[1] + 1 : b.a[1];
+            const unsigned long long av = sd == 2 ? 2 * b.a[2] + 1 : b.a[2];
+            const int K = ku > kv ? ku : kv;
+            keep_r = (au << (K - ku)) + (av << (K - kv)) <= (1ull << K);
+        }
+        const int c = hit ? (sd == 0 ? 2 : 1 + (keep_r ? 1 : 0)) : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {   // segmented inclusive scan of the children
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane - o >= st0) incl += y;
+        }
+        const bool ov = hit && (T.nn + T.np + incl > cap);
+        const unsigned As = __ballot_sync(FULL, ans) & segmask;
+        const unsigned Os = __ballot_sync(FULL, ov) & segmask;
+        const int A = As ? __ffs(As) - 1 : 32, O = Os ? __ffs(Os) - 1 : 32;
+        const int outcome = (A < 32 && A <= O) ? 1 : (O < 32 ? 2 : 0);
+        const unsigned long long at_fh = __shfl_sync(FULL, at, fh < 0 ? lane : fh);
+        const double w_fh = __shfl_sync(FULL, bt.w, fh < 0 ? lane : fh);
+        // t split: runs of equal t_L among the slot's colliding boxes; the
+        // first may continue the run left open by the previous iteration
+        const unsigned hb = Hs & ((1u << lane) - 1u);             // colliding boxes before me
+        const int ph = hb ? 31 - __clz(hb) : -1;
+        const unsigned long long at_ph = __shfl_sync(FULL, at, ph < 0 ? lane : ph);
+        const bool run_start = hit && (ph >= 0 ? at_ph != at : !(T.np > 0 && T.pend_at == at));
+        const unsigned Rs = __ballot_sync(FULL, run_start) & segmask;
+        const int lh = Hs ? 31 - __clz(Hs) : lane;
+        const unsigned long long at_lh = __shfl_sync(FULL, at, lh);
+        if (have && lane == A && outcome == 1) {
+            const unsigned long long if_at = T.found ? T.if_at : at_fh;
+            write_result(p, T.qi, 1, dmul(meta[so].qp.t_max, dyadic(if_at, T.k[0])), bt.w, n_L);
+            checks_done += (unsigned long long)n_L;
+        }
+        if (have && lane == en0 - 1) {   // the slot's last lane tells the owner
+            PoolAgg &G = sh.agg[so];
+            G.outcome = outcome;
+            G.fh = fh >= 0;
+            G.at_fh = at_fh;
+            G.w_fh = w_fh;
+            G.hits = __popc(Hs);
+            G.children = incl;
+            G.runs = __popc(Rs);
+            G.cnt0 = Rs ? __popc(Hs & ((1u << (__ffs(Rs) - 1)) - 1u)) : G.hits;
+            G.cntk = Rs ? __popc(Hs & ~((1u << (31 - __clz(Rs))) - 1u)) : G.hits;
+            G.at_k = at_lh;
+        }
+        __syncwarp();
+        // the owner moves the previous iteration's pending right children of
+        // a run that closes now into the level (before anyone writes pend)
+        const bool level_end = take > 0 && S.pos + take == S.size;
+        if (take > 0 && S.sd == 0 && S.np > 0 && sh.agg[lane].outcome == 0 &&
+            (sh.agg[lane].runs > 0 || level_end)) {
+            Box *nx = mine + (S.buf ? 0 : cap);
+            const Box *pd = mine + 2 * (size_t)cap;
+            for (int x = 0; x < S.np; ++x) nx[S.nn + sh.agg[lane].cnt0 + x] = pd[x];
+        }
+        __syncwarp();
+        if (hit && outcome == 0) {   // my children
+            Box *nx = sbase + (T.buf ? 0 : cap);
+            if (sd == 0) {
+                const unsigned upto = Rs & below;
+                const int j = __popc(upto);                               // my run (0: continued)
+                const int rs = upto ? 31 - __clz(upto) : st0;             // its first lane
+                const unsigned nxt_rs = Rs & ~below;
+                const int re = nxt_rs ? __ffs(nxt_rs) - 1 : 32;           // the next run's first lane
+                const unsigned runmask = (re == 32 ? 0xffffffffu : ((1u << re) - 1u)) &
+                                         ~((1u << rs) - 1u);
+                const int cnt = __popc(Hs & runmask);
+                const int i = __popc(hb & ~((1u << rs) - 1u));           // my rank in the run
+                const int h = __popc(hb);                                 // colliding boxes before me
+                const int P = T.np;
+                const bool closed = j < __popc(Rs) || (T.pos + (en0 - st0) == T.size);
+                nx[T.nn + (j > 0 ? P : 0) + 2 * h - i] = Box{{2 * at, b.a[1], b.a[2]}};
+                const Box r = Box{{2 * at + 1, b.a[1], b.a[2]}};
+                if (closed) nx[T.nn + P + 2 * (h - i) + cnt + i] = r;
+                else sbase[2 * (size_t)cap + (j == 0 ? P : 0) + i] = r;
+            } else {
+                Box l = b, r = b;
+#pragma unroll
+                for (int d = 1; d < 3; ++d) {
+                    l.a[d] = d == sd ? 2 * b.a[d] : b.a[d];
+                    r.a[d] = d == sd ? 2 * b.a[d] + 1 : b.a[d];
                 }
-                if (S.sd == 0) {
-                    if (S.np > 0 && S.pend_at != bb.a[0]) {
-                        for (int j = 0; j < S.np; ++j) nxt[S.nn + j] = pend[j];
-                        S.nn += S.np;
-                        S.np = 0;
-                    }
-                    if (S.nn + S.np + 2 > cap) { outcome = 2; break; }
-                    nxt[S.nn++] = Box{{2 * bb.a[0], bb.a[1], bb.a[2]}};
-                    pend[S.np++] = Box{{2 * bb.a[0] + 1, bb.a[1], bb.a[2]}};
-                    S.pend_at = bb.a[0];
-                } else {
-                    const int sd = S.sd;
-                    bool keep_r = true;
-                    if (KIND == CCD_KIND_VF) {
-                        const int ku = S.k[1] + (sd == 1), kv = S.k[2] + (sd == 2);
-                        const unsigned long long au = sd == 1 ? 2 * bb.a[1] + 1 : bb.a[1];
-                        const unsigned long long av = sd == 2 ? 2 * bb.a[2] + 1 : bb.a[2];
-                        const int K = ku > kv ? ku : kv;
-                        keep_r = (au << (K - ku)) + (av << (K - kv)) <= (1ull << K);
-                    }
-                    if (S.nn + 1 + (keep_r ? 1 : 0) > cap) { outcome = 2; break; }
-                    Box l = bb, r = bb;
-                    l.a[sd] = 2 * bb.a[sd];
-                    r.a[sd] = 2 * bb.a[sd] + 1;
-                    nxt[S.nn++] = l;
-                    if (keep_r) nxt[S.nn++] = r;
-                }
+                const long long pos = T.nn + incl - c;
+                nx[pos] = l;
+                if (keep_r) nx[pos + 1] = r;
             }
-            if (outcome == 1) {
-                checks_done += (unsigned long long)n;
+        }
+        __syncwarp();
+        // the owner updates its slot
+        if (take > 0) {
+            const PoolAgg G = sh.agg[lane];
+            if (!S.found && G.fh && G.outcome != 2) {
+                S.found = 1;
+                S.if_at = G.at_fh;
+                S.first_w = G.w_fh;
+            }
+            if (G.outcome == 1) {
                 S.qi = -1;
-            } else if (outcome == 2) {
+            } else if (G.outcome == 2) {
                 p.mid[atomicAdd(&p.hdr->mid, 1)] = (int)S.qi;
                 S.qi = -1;
             } else {
+                if (S.sd == 0) {
+                    if (level_end) {
+                        S.nn += S.np + 2 * G.hits;
+                        S.np = 0;
+                    } else if (G.runs == 0) {
+                        S.nn += G.hits;
+                        S.np += G.hits;
+                    } else {
+                        S.nn += S.np + 2 * G.hits - G.cntk;
+                        S.np = G.cntk;
+                        S.pend_at = G.at_k;
+                    }
+                } else {
+                    S.nn += G.children;
+                }
                 S.pos += take;
                 if (S.pos == S.size) {
-                    for (int j = 0; j < S.np; ++j) nxt[S.nn + j] = pend[j];
-                    S.nn += S.np;
-                    S.np = 0;
                     if (!S.found) {
                         write_result(p, S.qi, 0, __longlong_as_double(0x7ff0000000000000LL), 0.0,
                                      S.n_before + S.size);
@@ -1724,6 +1810,7 @@ __global__ void __launch_bounds__(32)
                         S.buf ^= 1;
                         S.size = S.nn;
                         S.nn = 0;
+                        S.np = 0;
                         S.k[S.sd] += 1;
                         S.pos = 0;
                         S.found = 0;
@@ -1796,14 +1883,17 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// slice_ns > 0 (deep stage of a served batch): the round ends slice_ns after
-// its first block started; a block takes no new query after that, so the SMs
-// come free for other batches' kernels, and the host launches another round
-// for the queries left in the list (no query is interrupted).
+// Rounds of a served batch's deep stage: a block takes no new query once
+// slice_ns has passed since the round's first block started (slice_ns > 0),
+// or once the host has set *yield (mapped host memory, read between
+// queries).  The SMs then come free for other batches' kernels, and the host
+// launches another round for the queries left in the list; no query is
+// interrupted and nothing waits.
 template <int BS, bool PAGED = false>
 __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
-                     long long cap, PagePool pool, long long slice_ns = 0)
+                     long long cap, PagePool pool, long long slice_ns = 0,
+                     const volatile int *yield = nullptr)
 {
     __shared__ Smem<BS> s;
     __shared__ int s_idx;
@@ -1821,7 +1911,8 @@ __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
     }
     for (;;) {
         if (threadIdx.x == 0) {
-            if (slice_ns > 0 && global_ns() - s_t0 > (unsigned long long)slice_ns)
+            if ((slice_ns > 0 && global_ns() - s_t0 > (unsigned long long)slice_ns) ||
+                (yield && *yield))
                 s_idx = 0x7fffffff;   // the round is over: leave the rest for the next one
             else
                 s_idx = atomicAdd(head, 1);
@@ -2800,25 +2891,27 @@ ccd_status multi_front(const MultiPlan &M, bool init_pool, cudaStream_t st)
 // The deep stage (paged), one round of at most slice_ns (0: until the list
 // is empty); or, for a contiguous layout, the whole deep stage.
 template <int DT>
-void multi_deep_launch(const MultiPlan &M, long long slice_ns, cudaStream_t st)
+void multi_deep_launch(const MultiPlan &M, long long slice_ns, const volatile int *yield,
+                       cudaStream_t st)
 {
     const size_t tq_deep = sizeof(SharedUV);
     if (M.D.paged)
         solve_kernel_seg<DT, true><<<M.D.nb_deep, DT, tq_deep, st>>>(
-            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns);
+            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
     else
         solve_kernel_seg<DT, false><<<M.D.nb_deep, DT, tq_deep, st>>>(
             M.p, M.segs, M.nseg, 1, (Box *)(M.ws + M.D.off_slots), M.D.cap_deep, PagePool{});
 }
 
-ccd_status multi_deep(const MultiPlan &M, long long slice_ns, cudaStream_t st)
+ccd_status multi_deep(const MultiPlan &M, long long slice_ns, const volatile int *yield,
+                      cudaStream_t st)
 {
     if (M.p.n == 0) return CCD_OK;
     if (slice_ns > 0 &&
         cudaMemsetAsync(&M.p.hdr->round_start, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return CCD_ERR_CUDA;
-    if (M.T.deep_threads == 256) multi_deep_launch<256>(M, slice_ns, st);
-    else multi_deep_launch<512>(M, slice_ns, st);
+    if (M.T.deep_threads == 256) multi_deep_launch<256>(M, slice_ns, yield, st);
+    else multi_deep_launch<512>(M, slice_ns, yield, st);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
 
@@ -2851,7 +2944,7 @@ ccd_status run_multi(const double *verts, int64_t n, const ccd_segment *segs, in
     cudaStream_t st = (cudaStream_t)stream;
     if ((r = multi_front(M, true, st)) != CCD_OK) return r;
     if (n == 0) return CCD_OK;
-    if ((r = multi_deep(M, 0, st)) != CCD_OK) return r;
+    if ((r = multi_deep(M, 0, nullptr, st)) != CCD_OK) return r;
     return multi_jumbo(M, st);
 }
 
@@ -2914,11 +3007,11 @@ ccd_status served_front(const ServedBatch &b, const FrontierPool &pool, cudaStre
 }
 
 ccd_status served_deep_round(const ServedBatch &b, const FrontierPool &pool, long long slice_ns,
-                             cudaStream_t st)
+                             const volatile int *yield, cudaStream_t st)
 {
     MultiPlan M;
     ccd_status r = plan(b, pool, &M);
-    return r != CCD_OK ? r : multi_deep(M, slice_ns, st);
+    return r != CCD_OK ? r : multi_deep(M, slice_ns, yield, st);
 }
 
 ccd_status served_finish(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st)
@@ -3167,14 +3260,15 @@ ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segm
 
 // ---- vertex-face batch on a static scratch array (no allocation) -------------
 //
-// For callers that cannot allocate device memory at all: code that runs
-// while a CUDA graph is being captured on its stream, real-time loops that
-// must not enter the driver's allocator, plugins running inside a host that
-// owns every allocation, or processes under a fixed device-memory quota.
-// They get one entry point whose scratch is a file-scope device array that
-// exists on every GPU that loads this library, until the process exits.
-// Its size bounds the batch: at most STATIC_MAX_N queries and a check limit
-// of at most STATIC_MAX_ITR per call.
+// For callers that cannot allocate device memory at all: real-time loops
+// that must not enter the driver's allocator, plugins running inside a host
+// that owns every allocation, or processes under a fixed device-memory
+// quota.  They get one entry point whose scratch is a file-scope device
+// array that exists on every GPU that loads this library, until the process
+// exits.  Its size bounds the batch: at most STATIC_MAX_N queries and a
+// check limit of at most STATIC_MAX_ITR per call; the one-warp stage has
+// slots for STATIC_SMALL_BLOCKS blocks and launches four per SM, at most
+// that many.
 
 #include <mutex>
 
@@ -3273,7 +3367,9 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
         cudaSuccess)
         return CCD_ERR_CUDA;
-    solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<STATIC_SMALL_BLOCKS, SMALL_THREADS, tq_small, st>>>(
+    int small_blocks = 4 * device_sms();
+    if (small_blocks < 1 || small_blocks > STATIC_SMALL_BLOCKS) small_blocks = STATIC_SMALL_BLOCKS;
+    solve_kernel<CCD_KIND_VF, SMALL_THREADS><<<small_blocks, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + STATIC_OFF_SMALL), STATIC_SMALL_CAP, PagePool{}, p.surv, &h->survivors,
         &h->head_small, p.over, nullptr, &h->overflow);
     solve_kernel<CCD_KIND_VF, DEEP_THREADS><<<STATIC_DEEP_SLOTS, DEEP_THREADS, tq_deep, st>>>(

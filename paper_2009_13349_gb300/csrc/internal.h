@@ -48,9 +48,10 @@ size_t served_workspace_bytes(int64_t n, int64_t max_itr_bound);
 size_t header_bytes();
 // header reset, validation, level 0, pooled and one-warp stages, deep list
 ccd_status served_front(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st);
-// one deep round of at most slice_ns (0: until the deep list is empty)
+// one deep round: until the deep list is empty, slice_ns has passed (> 0)
+// or *yield (device-readable host memory, may be NULL) is set
 ccd_status served_deep_round(const ServedBatch &b, const FrontierPool &pool, long long slice_ns,
-                             cudaStream_t st);
+                             const volatile int *yield, cudaStream_t st);
 // the deferred queries in the full-size slots
 ccd_status served_finish(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st);
 // from a host copy of the batch's header: deep queries not yet taken, and

@@ -19,13 +19,17 @@
 // whole |F| <= d regions and are batched apart), contiguous in the inbox.  On
 // its stream the descriptors are gathered into the batch's segment table and
 // the records turned into planes (both on the device), eps is taken from each
-// request's own bounds (Sec. 6), and the solver stages run.  The deep stage
-// runs in time-sliced rounds: its blocks take no new query once a round's
-// slice has passed, which frees the SMs for other lanes' kernels (lanes of
-// cheap batches have the higher stream priority), and poll() launches the next
-// round.  Nothing on the device waits for anything.  Each request's answer is
-// the one a call of its own would give: the solver's results do not depend on
-// batching, launch shapes, pool size or round boundaries.
+// request's own bounds (Sec. 6), and the solver stages run.  Expensive
+// batches run one at a time, in arrival order, on the last lane, at the low
+// stream priority; the others run on the remaining lanes at the high one.
+// The deep stage runs in rounds: when a cheap batch starts while an
+// expensive one is in its deep stage, the latter's blocks are asked (a flag
+// in mapped host memory) to take no new query, which frees the SMs for the
+// cheap batch's kernels, and poll() launches the next round; optionally
+// rounds also end after a fixed slice.  Nothing on the device waits for
+// anything.  Each request's answer is the one a call of its own would give:
+// the solver's results do not depend on batching, launch shapes, pool size
+// or round boundaries.
 
 #include "ccd.h"
 #include "internal.h"
@@ -81,6 +85,8 @@ struct Lane {
     int64_t *h_chk;
     unsigned char *h_hdr;
     cudaEvent_t ev;
+    volatile int *yield;      // mapped host memory: set to end the running deep round
+    int *d_yield;             // its device address
 };
 
 // descriptors of requests first_slot .. first_slot + k - 1 (ring order) into
@@ -129,8 +135,12 @@ void fill_defaults(ccd_server_config &c)
     if (c.max_requests == 0) c.max_requests = 4096;
     if (c.max_segments == 0) c.max_segments = 1024;
     if (c.max_itr_bound == 0) c.max_itr_bound = 1000000;
-    if (c.deep_slice_us == 0) c.deep_slice_us = 20000;
 }
+
+// An expensive batch (class 1) holds up to this many queries: enough deep
+// queries to fill the GPU, few enough that its first request is not kept long
+// waiting for the others.
+constexpr int64_t MAX_BATCH_EXPENSIVE = 65536;
 
 size_t lane_bytes(const ccd_server_config &c)
 {
@@ -158,7 +168,7 @@ bool form_batch(ccd_server *S, Lane &L)
 {
     size_t first = 0, count = 0;
     if (!ccd_serve::select_batch(S->order, L.high, S->cfg.max_batch, S->cfg.max_segments, &first,
-                                 &count))
+                                 &count, MAX_BATCH_EXPENSIVE))
         return false;
     std::vector<Req *> take(S->order.begin() + first, S->order.begin() + first + count);
     int64_t n = 0;
@@ -188,7 +198,9 @@ bool form_batch(ccd_server *S, Lane &L)
     ccd_status r = ccd_aos_to_soa(S->inbox + (size_t)base * 24, n, L.verts, n, st);
     if (r == CCD_OK) r = ccd_segments_err_from_bounds(L.verts, n, L.segs, k, st);
     if (r == CCD_OK) r = served_front(b, S->pool, st);
-    if (r == CCD_OK) r = served_deep_round(b, S->pool, S->cfg.deep_slice_us * 1000LL, st);
+    *L.yield = 0;
+    if (r == CCD_OK)
+        r = served_deep_round(b, S->pool, S->cfg.deep_slice_us * 1000LL, L.d_yield, st);
     if (r == CCD_OK &&
         cudaMemcpyAsync(L.h_hdr, b.workspace, header_bytes(), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess)
@@ -217,7 +229,8 @@ void advance(ccd_server *S, Lane &L)
     if (L.state == 1) {
         ccd_status r = CCD_OK;
         if (served_deep_left(L.h_hdr) > 0) {   // another round for the rest of the deep list
-            r = served_deep_round(L.b, S->pool, S->cfg.deep_slice_us * 1000LL, st);
+            *L.yield = 0;
+            r = served_deep_round(L.b, S->pool, S->cfg.deep_slice_us * 1000LL, L.d_yield, st);
             if (r == CCD_OK &&
                 cudaMemcpyAsync(L.h_hdr, L.b.workspace, header_bytes(), cudaMemcpyDeviceToHost,
                                 st) != cudaSuccess)
@@ -276,11 +289,24 @@ void progress(ccd_server *S)
     for (int l = 0; l < S->cfg.lanes; ++l) advance(S, S->lanes[l]);
     release_front(S);
     // high-priority lanes first: cheap requests should not queue behind
-    // expensive ones
+    // expensive ones.  A new cheap batch asks the deep rounds running on the
+    // low-priority lane to end, so that its kernels get SMs (the next round
+    // follows at the next poll, at low priority).
+    bool cheap_started = false, running[MAX_LANES];
+    for (int l = 0; l < S->cfg.lanes; ++l) running[l] = S->lanes[l].state == 1;
     for (int pass = 0; pass < 2; ++pass)
         for (int l = 0; l < S->cfg.lanes; ++l) {
             Lane &L = S->lanes[l];
-            if (L.state == 0 && L.high == (pass == 0)) form_batch(S, L);
+            if (L.state == 0 && L.high == (pass == 0) && form_batch(S, L) && L.high)
+                cheap_started = true;
+        }
+    if (cheap_started)
+        for (int l = 0; l < S->cfg.lanes; ++l) {
+            Lane &L = S->lanes[l];
+            if (!L.high && running[l] && L.state == 1 && !*L.yield) {
+                *L.yield = 1;
+                S->stats.yields += 1;
+            }
         }
     int busy = 0;
     for (int l = 0; l < S->cfg.lanes; ++l) busy += S->lanes[l].state != 0;
@@ -300,6 +326,7 @@ void destroy(ccd_server *S)
         if (L.st) cudaStreamDestroy(L.st);
         if (L.ev) cudaEventDestroy(L.ev);
         if (L.h_col) cudaFreeHost(L.h_col);
+        if (L.yield) cudaFreeHost((void *)L.yield);
     }
     if (S->upload) cudaStreamDestroy(S->upload);
     if (S->h_ring) cudaFreeHost(S->h_ring);
@@ -350,7 +377,7 @@ ccd_status ccd_batch_begin(const ccd_server_config *config, ccd_server **out)
     const size_t n = (size_t)c.max_batch;
     for (int l = 0; l < c.lanes; ++l) {
         Lane &L = S->lanes[l];
-        L.high = l < (c.lanes + 1) / 2;
+        L.high = l < c.lanes - 1;   // the last lane takes expensive batches, one at a time
         if (cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, L.high ? hi : lo) !=
                 cudaSuccess ||
             cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -375,6 +402,15 @@ ccd_status ccd_batch_begin(const ccd_server_config *config, ccd_server **out)
         L.h_tol = (double *)hc; hc += al256(8 * n);
         L.h_chk = (int64_t *)hc; hc += al256(8 * n);
         L.h_hdr = (unsigned char *)hc;
+        void *y = nullptr;
+        if (cudaHostAlloc(&y, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&L.d_yield, y, 0) != cudaSuccess) {
+            if (y) cudaFreeHost(y);
+            destroy(S);
+            return CCD_ERR_CUDA;
+        }
+        L.yield = (volatile int *)y;
+        *L.yield = 0;
     }
     a += (size_t)c.lanes * lb;
     S->pool.bits = (unsigned long long *)a;

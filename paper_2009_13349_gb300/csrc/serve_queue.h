@@ -42,25 +42,29 @@ int64_t inbox_alloc(const Q &order, int64_t cap, int64_t want)
 // The next batch for a lane: a high-priority lane takes the oldest waiting
 // request of class 0, any other lane the oldest waiting request; the batch
 // extends over the following requests while they wait, share its class, lie
-// right after it in the inbox and fit max_batch records and max_segments
-// requests.  Returns false when nothing waits for this lane; otherwise the
-// batch is order[*first .. *first + *count).
+// right after it in the inbox and fit max_batch records (class 1: at most
+// max_batch_1, but at least one request) and max_segments requests.
+// Returns false when nothing waits for this lane; otherwise the batch is
+// order[*first .. *first + *count).
 template <class Q>
 bool select_batch(const Q &order, bool high, int64_t max_batch, int max_segments, size_t *first,
-                  size_t *count)
+                  size_t *count, int64_t max_batch_1 = -1)
 {
     size_t i = 0;
     for (; i < order.size(); ++i)
         if (order[i]->state == WAITING && (!high || order[i]->cls == 0)) break;
     if (i == order.size()) return false;
     const int cls = order[i]->cls;
+    const int64_t limit = cls == 1 && max_batch_1 >= 0 ? max_batch_1 : max_batch;
     const size_t i0 = i;
     int64_t n = 0;
     for (; i < order.size(); ++i) {
         const auto *r = order[i];
         if (r->state != WAITING || r->cls != cls) break;
         if (i > i0 && r->off != order[i - 1]->off + order[i - 1]->n) break;   // ring wrapped
-        if (n + r->n > max_batch || (int64_t)(i - i0) >= max_segments) break;
+        if ((i > i0 && n + r->n > limit) || n + r->n > max_batch ||
+            (int64_t)(i - i0) >= max_segments)
+            break;
         n += r->n;
     }
     if (i == i0) return false;

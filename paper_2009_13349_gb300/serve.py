@@ -43,7 +43,7 @@ class Server:
     """One C server (see include/ccd.h, "The served form")."""
 
     def __init__(self, budget: int = 40 << 30, lanes: int = 4, max_batch: int = 1 << 20,
-                 max_itr_bound: int = 10**6, deep_slice_us: int = 20_000, clock=time.perf_counter,
+                 max_itr_bound: int = 10**6, deep_slice_us: int = 0, clock=time.perf_counter,
                  **config):
         from . import ccd
         self.native = ccd.NativeServer(budget_bytes=int(budget), lanes=int(lanes),

@@ -6,7 +6,7 @@ ms in {0, 1e-4}, m_I = 1e6.
 Every request's answer must equal the oracle's (on a sample of its queries;
 eps from the request's own bounds, Sec. 6) and the answer of a call of its
 own, while several batches are in flight at once and the deep stage runs in
-time-sliced rounds.
+rounds (ended by a fixed slice, or when a cheap batch needs the SMs).
 """
 import os
 
@@ -49,6 +49,7 @@ def test_served_requests_equal_oracle_and_their_own_calls():
     from paper_2009_13349_gb300.serve import Server
     reqs = _requests(28, 100, 20_000, seed=51)
     srv = Server(budget=12 << 30, lanes=4, max_batch=40_000, deep_slice_us=5_000)
+    # deep rounds of at most 5 ms, besides the rounds cheap batches end
     for r in reqs:
         assert srv.submit(r)
     srv.drain()
@@ -80,6 +81,40 @@ def test_served_requests_equal_oracle_and_their_own_calls():
             assert np.array_equal(x[idx], y), f"request {r.id}: served differs from the oracle"
 
 
+def test_cheap_batches_end_expensive_deep_rounds():
+    """Expensive requests (ms > delta) run on the low-priority lane; cheap
+    ones submitted while its deep stage runs make its rounds end (no fixed
+    slice here), and every answer still equals the request's own call."""
+    from paper_2009_13349_gb300 import ccd
+    from paper_2009_13349_gb300.serve import Request, Server
+    rng = np.random.default_rng(71)
+    heavy = [Request(i, i % 2, W.unit_cube(i % 2, 6000, seed=700 + i).verts, delta=1e-6,
+                     ms=1e-4) for i in range(2)]
+    light = [Request(10 + i, i % 2, W.unit_cube(i % 2, int(rng.integers(200, 3000)),
+                                                 seed=710 + i).verts, delta=1e-6, ms=0.0)
+             for i in range(12)]
+    srv = Server(budget=8 << 30, lanes=3, max_batch=20_000)
+    for r in heavy:
+        assert srv.submit(r)
+    for r in light:                      # arrive while the heavy batch runs
+        srv.poll(wait_us=2000)
+        assert srv.submit(r)
+    srv.drain()
+    st = srv.stats()
+    srv.close()
+    assert st["yields"] > 0 and st["deep_rounds"] > st["batches"]
+    assert max(r.done for r in light) < max(r.done for r in heavy)
+    for r in heavy + light:
+        assert r.status == 0
+        v = ccd.to_soa(r.aos)
+        e = ccd.err_from_bounds(r.kind, v, ms_nonzero=r.ms > 0)
+        alone = ccd.batch(r.kind, v, e, ms=r.ms, delta=r.delta, max_itr=r.max_itr)
+        torch.cuda.synchronize()
+        for x, y in zip((r.collides, r.toi, r.out_tol, r.checks),
+                        (alone.collides, alone.toi, alone.out_tol, alone.checks)):
+            assert np.array_equal(x, y.cpu().numpy()), f"request {r.id}"
+
+
 def test_served_backpressure_cancel_and_refusals():
     from paper_2009_13349_gb300 import ccd
     from paper_2009_13349_gb300.serve import Request, Server
@@ -102,7 +137,8 @@ def test_served_backpressure_cancel_and_refusals():
         srv.submit(Request(98, 0, np.zeros((10, 24)), max_itr=10**7))
     srv.drain()
     # the rest go in as room frees up; cancel the last one while it waits
-    rest = [r for r in reqs if r not in taken]
+    taken_ids = {r.id for r in taken}
+    rest = [r for r in reqs if r.id not in taken_ids]
     tickets = {}
     for r in rest:
         while not srv.submit(r):
