@@ -112,7 +112,9 @@ struct Header {
     unsigned long long round_start; // %globaltimer at the start of a time-sliced deep round
     unsigned long long pool_iters;  // iterations of the pooled solver's warps
     unsigned long long pool_serial; // sum over those of the most boxes one slot placed
-    int pad[8];
+    int overflow_ee;  // segmented batches: edge-edge queries in the deep list ...
+    int head_deep_ee; // ... and their work counter (vertex-face: overflow, head_deep)
+    int pad[6];
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte line");
 
@@ -560,6 +562,9 @@ struct Params {
     int *over;       // one-warp solver hand-offs   -> deep solver
     unsigned char *over_level;   // level at which each hand-off outgrew its slot
     int *deep_list;  // `over` ordered by that level, shallowest first
+    int *over_ee;    // segmented batches: the edge-edge hand-offs, apart
+    unsigned char *over_level_ee;
+    int *deep_list_ee;
     int *jumbo;      // deep queries deferred for lack of frontier pages
     double *kappa;
 };
@@ -1873,9 +1878,12 @@ __global__ void __launch_bounds__(ROOT_THREADS)
     else root_query<CCD_KIND_EE>(p, i, q);
 }
 
-// deep: 0 = one-warp stage (list `mid`), 1 = deep stage (deep_list; PAGED:
-// frontier pages from `pool`, queries without pages deferred to `jumbo`),
-// 2 = full-size stage (the deferred queries).
+// deep: 0 = one-warp stage (list `mid`; hand-offs go to the deep list of
+// their kind), 1 = deep stage (PAGED: frontier pages from `pool`, queries
+// without pages deferred to `jumbo`), 2 = full-size stage (the deferred
+// queries).  KS >= 0: the kernel solves queries of that kind only (the deep
+// stage runs one launch per kind, each with the registers of one kind and
+// so three blocks per SM); KS < 0: either kind.
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -1889,8 +1897,10 @@ __device__ __forceinline__ unsigned long long global_ns()
 // queries).  The SMs then come free for other batches' kernels, and the host
 // launches another round for the queries left in the list; no query is
 // interrupted and nothing waits.
-template <int BS, bool PAGED = false>
-__global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
+template <int BS, bool PAGED = false, int KS = -1>
+__global__ void __launch_bounds__(BS, BS == 256 ? (KS >= 0 ? DEEP_BLOCKS_PER_SM
+                                                            : SEG_DEEP_BLOCKS_PER_SM)
+                                               : 1)
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
                      long long cap, PagePool pool, long long slice_ns = 0,
                      const volatile int *yield = nullptr)
@@ -1901,9 +1911,14 @@ __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
     extern __shared__ double tq[];   // [2 * BS][TWidth<EE>::W]: sized for either kind
     Box *cur = slots + (size_t)blockIdx.x * 2 * (size_t)cap;
     Box *nxt = cur + cap;
-    const int *list = deep == 2 ? p.jumbo : deep ? p.deep_list : p.mid;
-    const int *count = deep == 2 ? &p.hdr->jumbo : deep ? &p.hdr->overflow : &p.hdr->mid;
-    int *head = deep == 2 ? &p.hdr->head_jumbo : deep ? &p.hdr->head_deep : &p.hdr->head_small;
+    const bool ee = KS == CCD_KIND_EE;
+    const int *list = deep == 2 ? p.jumbo : deep ? (ee ? p.deep_list_ee : p.deep_list) : p.mid;
+    const int *count = deep == 2 ? &p.hdr->jumbo
+                       : deep    ? (ee ? &p.hdr->overflow_ee : &p.hdr->overflow)
+                                 : &p.hdr->mid;
+    int *head = deep == 2 ? &p.hdr->head_jumbo
+                : deep    ? (ee ? &p.hdr->head_deep_ee : &p.hdr->head_deep)
+                          : &p.hdr->head_small;
     if (slice_ns > 0 && threadIdx.x == 0) {
         const unsigned long long now = global_ns();
         const unsigned long long t0 = atomicCAS(&p.hdr->round_start, 0ull, now);
@@ -1922,25 +1937,44 @@ __global__ void __launch_bounds__(BS, BS == 256 ? SEG_DEEP_BLOCKS_PER_SM : 1)
         __syncthreads();
         if (idx >= *(volatile const int *)count) return;
         const long long qi = list[idx];
-        const ccd_segment sg = segs[find_segment(segs, nseg, qi)];
-        const QP q = qp_segment(sg);
+        // the query's parameters, block-uniform, in shared memory (they
+        // would otherwise hold registers through the whole solve)
+        __shared__ QP q;
+        __shared__ int s_kind;
+        if (threadIdx.x == 0) {
+            const ccd_segment &sg = segs[find_segment(segs, nseg, qi)];
+            q = qp_segment(sg);
+            s_kind = sg.kind;
+        }
+        __syncthreads();
+        const int kind = s_kind;
         int level = 0;
         bool done;
         if constexpr (PAGED) {
             __shared__ PageTables pt;
             PagedFrontier<BS> F{pool, &pt};
-            done = sg.kind == CCD_KIND_VF
-                       ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, false, s, tq, level)
-                       : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, false, s, tq, level);
+            if constexpr (KS >= 0)
+                done = solve_query<(KS >= 0 ? KS : 0), BS>(p, q, qi, F, false, s, tq, level);
+            else
+                done = kind == CCD_KIND_VF
+                           ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, false, s, tq, level)
+                           : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, false, s, tq, level);
         } else {
             ContigFrontier<BS> F{cur, nxt, cap};
-            done = sg.kind == CCD_KIND_VF
-                       ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, deep != 0, s, tq, level)
-                       : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, deep != 0, s, tq, level);
+            if constexpr (KS >= 0)
+                done = solve_query<(KS >= 0 ? KS : 0), BS>(p, q, qi, F, deep != 0, s, tq, level);
+            else
+                done = kind == CCD_KIND_VF
+                           ? solve_query<CCD_KIND_VF, BS>(p, q, qi, F, deep != 0, s, tq, level)
+                           : solve_query<CCD_KIND_EE, BS>(p, q, qi, F, deep != 0, s, tq, level);
         }
         if (!done && threadIdx.x == 0) {
-            if (deep) {                  // paged deep stage: deferred to a full-size slot
+            if (KS >= 0 || deep) {       // paged deep stage: deferred to a full-size slot
                 p.jumbo[atomicAdd(&p.hdr->jumbo, 1)] = (int)qi;
+            } else if (kind == CCD_KIND_EE) {
+                const int j = atomicAdd(&p.hdr->overflow_ee, 1);
+                p.over_ee[j] = (int)qi;
+                p.over_level_ee[j] = (unsigned char)level;
             } else {
                 const int j = atomicAdd(&p.hdr->overflow, 1);
                 p.over[j] = (int)qi;
@@ -2485,6 +2519,9 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
     p.over = (int *)(ws + L.off_over);
     p.over_level = (unsigned char *)(ws + L.off_level);
     p.deep_list = (int *)(ws + L.off_dlist);
+    p.over_ee = nullptr;
+    p.over_level_ee = nullptr;
+    p.deep_list_ee = nullptr;
     p.jumbo = (int *)(ws + L.off_jlist);
     p.kappa = (double *)(ws + L.off_kappa);
     Header *h = p.hdr;
@@ -2734,7 +2771,7 @@ struct Tuned {
 
 bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
 {
-    Tuned r{DEEP_THREADS, SEG_DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
+    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
     if (t) {
         if (t->deep_threads) r.deep_threads = t->deep_threads;
         if (t->deep_slots) r.deep_slots = t->deep_slots;
@@ -2758,6 +2795,9 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
     off = align256(off + sizeof(int) * (size_t)n);          // overflow
     off = align256(off + (size_t)n);                        // overflow levels
     off = align256(off + sizeof(int) * (size_t)n);          // deep list
+    off = align256(off + sizeof(int) * (size_t)n);          // edge-edge overflow
+    off = align256(off + (size_t)n);                        // its levels
+    off = align256(off + sizeof(int) * (size_t)n);          // edge-edge deep list
     off = align256(off + sizeof(int) * (size_t)n);          // deferred (full-size) list
     off = align256(off + 3 * sizeof(double) * (size_t)n);  // kappa
     off = align256(off + sizeof(Box) * 3 * (size_t)T.pool_cap * POOL_SLOTS *
@@ -2825,6 +2865,9 @@ ccd_status multi_plan(const double *verts, int64_t n, const ccd_segment *segs, i
     p.over = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.over_level = (unsigned char *)(ws + off); off = align256(off + (size_t)n);
     p.deep_list = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.over_ee = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
+    p.over_level_ee = (unsigned char *)(ws + off); off = align256(off + (size_t)n);
+    p.deep_list_ee = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.jumbo = (int *)(ws + off); off = align256(off + sizeof(int) * (size_t)n);
     p.kappa = (double *)(ws + off); off = align256(off + 3 * sizeof(double) * (size_t)n);
     m.pool_mem = (Box *)(ws + off);
@@ -2848,7 +2891,10 @@ template <int DT>
 ccd_status set_deep_attributes()
 {
     const size_t tq_deep = sizeof(SharedUV);
-    for (auto *k : {solve_kernel_seg<DT, true>, solve_kernel_seg<DT, false>})
+    for (auto *k : {solve_kernel_seg<DT, true>, solve_kernel_seg<DT, false>,
+                    solve_kernel_seg<DT, true, CCD_KIND_VF>, solve_kernel_seg<DT, true, CCD_KIND_EE>,
+                    solve_kernel_seg<DT, false, CCD_KIND_VF>,
+                    solve_kernel_seg<DT, false, CCD_KIND_EE>})
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
             cudaSuccess)
             return CCD_ERR_CUDA;
@@ -2884,6 +2930,8 @@ ccd_status multi_front(const MultiPlan &M, bool init_pool, cudaStream_t st)
     solve_kernel_seg<SMALL_THREADS, false><<<M.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, M.segs, M.nseg, 0, (Box *)(M.ws + M.off_small), M.T.small_cap, PagePool{});
     order_by_level_kernel<<<1, 1024, 0, st>>>(p.over, p.over_level, &p.hdr->overflow, p.deep_list);
+    order_by_level_kernel<<<1, 1024, 0, st>>>(p.over_ee, p.over_level_ee, &p.hdr->overflow_ee,
+                                              p.deep_list_ee);
     stage_mark(3, st);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
@@ -2895,12 +2943,18 @@ void multi_deep_launch(const MultiPlan &M, long long slice_ns, const volatile in
                        cudaStream_t st)
 {
     const size_t tq_deep = sizeof(SharedUV);
-    if (M.D.paged)
-        solve_kernel_seg<DT, true><<<M.D.nb_deep, DT, tq_deep, st>>>(
+    Box *slots = (Box *)(M.ws + M.D.off_slots);
+    if (M.D.paged) {
+        solve_kernel_seg<DT, true, CCD_KIND_VF><<<M.D.nb_deep, DT, tq_deep, st>>>(
             M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
-    else
-        solve_kernel_seg<DT, false><<<M.D.nb_deep, DT, tq_deep, st>>>(
-            M.p, M.segs, M.nseg, 1, (Box *)(M.ws + M.D.off_slots), M.D.cap_deep, PagePool{});
+        solve_kernel_seg<DT, true, CCD_KIND_EE><<<M.D.nb_deep, DT, tq_deep, st>>>(
+            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
+    } else {
+        solve_kernel_seg<DT, false, CCD_KIND_VF><<<M.D.nb_deep, DT, tq_deep, st>>>(
+            M.p, M.segs, M.nseg, 1, slots, M.D.cap_deep, PagePool{});
+        solve_kernel_seg<DT, false, CCD_KIND_EE><<<M.D.nb_deep, DT, tq_deep, st>>>(
+            M.p, M.segs, M.nseg, 1, slots, M.D.cap_deep, PagePool{});
+    }
 }
 
 ccd_status multi_deep(const MultiPlan &M, long long slice_ns, const volatile int *yield,
@@ -3024,7 +3078,8 @@ ccd_status served_finish(const ServedBatch &b, const FrontierPool &pool, cudaStr
 long long served_deep_left(const void *header)
 {
     const Header *h = (const Header *)header;
-    return h->head_deep >= h->overflow ? 0 : (long long)(h->overflow - h->head_deep);
+    return (h->head_deep >= h->overflow ? 0 : (long long)(h->overflow - h->head_deep)) +
+           (h->head_deep_ee >= h->overflow_ee ? 0 : (long long)(h->overflow_ee - h->head_deep_ee));
 }
 
 int served_status(const void *header) { return ((const Header *)header)->status; }
@@ -3355,6 +3410,9 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     p.over = (int *)(ws + STATIC_OFF_OVER);
     p.over_level = nullptr;   // no deep-tier ordering in the static-scratch path
     p.deep_list = nullptr;
+    p.over_ee = nullptr;
+    p.over_level_ee = nullptr;
+    p.deep_list_ee = nullptr;
     p.jumbo = nullptr;
     p.kappa = (double *)(ws + STATIC_OFF_KAPPA);
     Header *h = p.hdr;
