@@ -233,7 +233,7 @@ typedef struct {
  * Launch shapes of the solver kernels.  They change speed only: results are
  * identical for every valid tuning.  A zero field takes the default.
  *  deep_threads         threads of a deep-solver block, 256 or 512 (256)
- *  deep_slots           deep-solver blocks / frontier slots (two per SM)
+ *  deep_slots           deep-solver blocks per kind (three per SM)
  *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
  *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
  *  pool_cap             boxes per level a query may reach in the pooled

@@ -10,7 +10,7 @@ and workload tag in a JSON file (``$CCD_TUNING_CACHE`` or
 Tunables (see include/ccd.h):
   deep_threads         block size of the deep solver (256 or 512)
   deep_slots           deep-solver blocks, i.e. queries with large frontiers
-                       solved at once (0 = one per SM)
+                       solved at once (0 = three per SM)
   small_blocks_per_sm  one-warp solver blocks per SM (its queue width)
   small_cap            frontier depth of a one-warp solver slot in boxes
   pool_cap             boxes per level a query may reach in the pooled solver
@@ -27,10 +27,10 @@ FIELDS = ("deep_threads", "deep_slots", "small_blocks_per_sm", "small_cap", "poo
 
 def candidates(sms: int) -> list[dict]:
     out = []
-    for dt, slots in ((256, 2 * sms), (512, sms), (256, sms)):
+    for dt, slots in ((256, 3 * sms), (256, 2 * sms), (512, sms)):
         for sb in (8, 16):
             for cap in (256, 1024):
-                for pc in (64, 1024):
+                for pc in (64, 256):
                     out.append({"deep_threads": dt, "deep_slots": slots,
                                 "small_blocks_per_sm": sb, "small_cap": cap, "pool_cap": pc})
     return out
