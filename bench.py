@@ -70,8 +70,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--n", type=int, default=None,
+                    help="simulation-mixed (default 1,000,000) / degenerate-heavy (100,000) / "
+                         "line-search queries")
+    ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--ref-sample", type=int, default=40_000)
     ap.add_argument("--max-itr", type=int, default=10**6,
@@ -82,8 +84,8 @@ def parse():
                     help="simulation-mixed: frontier pages of the deep tier (smaller workspace, "
                          "e.g. for profiling)")
     ap.add_argument("--workload", default="multi-instance",
-                    choices=["simulation-mixed", "multi-instance", "served", "line-search",
-                             "active-set"])
+                    choices=["simulation-mixed", "degenerate-heavy", "multi-instance", "served",
+                             "line-search", "active-set"])
     ap.add_argument("--scale", type=float, default=1.0,
                     help="multi-instance/served: fraction of the full query count")
     ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
@@ -92,13 +94,22 @@ def parse():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="multi-instance: the default launch shapes instead of the autotuner's")
+    ap.add_argument("--tuning", default=None,
+                    help="multi-instance: launch shapes as JSON (deep_threads, deep_slots, "
+                         "small_blocks_per_sm, small_cap, pool_cap) instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true",
                     help="multi-instance: skip the plain-form and simulation-mixed comparisons "
                          "that follow the timed region (small profiling cases)")
     ap.add_argument("--nx", type=int, default=512, help="active-set: vertices per sheet side")
     ap.add_argument("--compare-printed-cap", action="store_true",
                     help="line-search: also time d = max(p d_i, delta) (about a minute a step)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    heavy = args.workload == "degenerate-heavy"
+    if args.n is None:
+        args.n = 100_000 if heavy else 1_000_000
+    if args.seed is None:
+        args.seed = 2 if heavy else 1
+    return args
 
 
 def dist_env():
@@ -225,29 +236,53 @@ def make_workload(n, seed):
     return W.simulation_mixed(n=n, seed=seed)
 
 
-def cpu_baseline(batches, sample: int, seed: int = 123, max_itr: int = 10**6):
+def make_jobs(args, seed):
+    """The calls of one step: (batch, ms) pairs.  simulation-mixed: both kinds
+    at ms = 0; degenerate-heavy: both kinds at ms = 0 and at ms = 1e-4."""
+    from paper_2009_13349_gb300 import workloads as W
+    if args.workload == "degenerate-heavy":
+        wl = W.degenerate_heavy(n=args.n, seed=seed)
+        return wl, [(b, ms) for ms in (0.0, 1e-4) for b in wl.batches]
+    wl = make_workload(args.n, seed)
+    return wl, [(b, 0.0) for b in wl.batches]
+
+
+def job_label(b, ms):
+    return ("VF" if b.kind == 0 else "EE") + ("" if ms == 0 else f" ms={ms:g}")
+
+
+def cpu_baseline(batches, sample: int, seed: int = 123, max_itr: int = 10**6, ms=None):
     """Oracle on a bounded random sample of the batches (sizes proportional),
-    each batch with its own scene eps, all host cores."""
+    each batch with its own scene eps (and minimum separation ms[i]), all
+    host cores."""
     import oracle
     rng = np.random.default_rng(seed)
     cores = os.cpu_count() or 1
     total = sum(b.n for b in batches)
+    ms = ms or [0.0] * len(batches)
     picks = []
-    for b in batches:
+    for b, m in zip(batches, ms):
         k = min(b.n, max(1, int(round(sample * b.n / total))))
-        picks.append((b, np.sort(rng.choice(b.n, k, replace=False))))
+        picks.append((b, m, np.sort(rng.choice(b.n, k, replace=False))))
     total_q, total_s = 0, 0.0
-    for b, idx in picks:
-        err = oracle.err_from_bounds(b.kind, b.verts)      # eps of the whole instance
+    for b, m, idx in picks:
+        err = oracle.err_from_bounds(b.kind, b.verts, ms_nonzero=m > 0)   # whole-instance eps
         t0 = time.perf_counter()
-        oracle.ccd_batch(b.kind, b.verts[idx], err, delta=1e-6, max_itr=max_itr, nthreads=cores)
+        oracle.ccd_batch(b.kind, b.verts[idx], err, ms=m, delta=1e-6, max_itr=max_itr,
+                         nthreads=cores)
         total_s += time.perf_counter() - t0
         total_q += idx.size
     return total_q / total_s, cores, total_s, total_q
 
 
 def workload_config(args):
-    """The simulation-mixed workload's config keys."""
+    """The simulation-mixed (or degenerate-heavy) workload's config keys."""
+    if args.workload == "degenerate-heavy":
+        return {"workload": f"degenerate-heavy {args.n} queries per GPU (VF:EE 1:1; coplanar, "
+                            f"collinear, parallel-edge, vertex-on-vertex and grazing-tangent "
+                            f"motions on a 2^-20 grid), seed {args.seed}, each step at ms = 0 "
+                            f"and at ms = 1e-4",
+                "delta": 1e-6, "max_itr": args.max_itr, "ms": [0.0, 1e-4]}
     return {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
             "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0}
 
@@ -328,8 +363,8 @@ def measure_simulation_mixed(args, dev, steps, warmup, seed, stage_detail=True):
     timing, stage and roofline figures and the buffers for the caller."""
     import torch
     from paper_2009_13349_gb300 import ccd
-    wl = make_workload(args.n, seed)
-    batches = wl.batches
+    wl, jobs = make_jobs(args, seed)
+    batches = [b for b, _ in jobs]
     verts = [ccd.to_soa(b.verts, dev) for b in batches]
     ws = [ccd.workspace(b.n, args.max_itr, dev, pages=args.pages) for b in batches]
     res = [ccd.Result(torch.empty(b.n, dtype=torch.uint8, device=dev),
@@ -342,14 +377,14 @@ def measure_simulation_mixed(args, dev, steps, warmup, seed, stage_detail=True):
     side = [torch.cuda.Stream(dev) for _ in batches]
 
     def step(stage_sets=None):
-        for j, b in enumerate(batches):
+        for j, (b, ms) in enumerate(jobs):
             side[j].wait_stream(stream)
             with torch.cuda.stream(side[j]):
                 if stage_sets is not None:
                     ccd.set_stage_events(stage_sets[j])
-                err = ccd.err_from_bounds(b.kind, verts[j], stream=side[j])
-                ccd.batch(b.kind, verts[j], err, delta=1e-6, max_itr=args.max_itr, ws=ws[j],
-                          out=res[j], stream=side[j])
+                err = ccd.err_from_bounds(b.kind, verts[j], ms_nonzero=ms > 0, stream=side[j])
+                ccd.batch(b.kind, verts[j], err, ms=ms, delta=1e-6, max_itr=args.max_itr,
+                          ws=ws[j], out=res[j], stream=side[j])
         ccd.set_stage_events(None)
         for sj in side:
             stream.wait_stream(sj)
@@ -366,15 +401,16 @@ def measure_simulation_mixed(args, dev, steps, warmup, seed, stage_detail=True):
     stage_sets = [[[new_event() for _ in range(5)] for _ in batches] for _ in range(steps)]
     marks = [new_event() for _ in range(steps + 1)]
     torch.cuda.synchronize(dev)
-    return {"wl": wl, "verts": verts, "ws": ws, "res": res, "side": side, "stream": stream,
-            "step": step, "stage_sets": stage_sets, "marks": marks}
+    return {"wl": wl, "jobs": jobs, "batches": batches, "verts": verts, "ws": ws, "res": res,
+            "side": side, "stream": stream, "step": step, "stage_sets": stage_sets,
+            "marks": marks}
 
 
 def simulation_mixed_figures(args, S, steps, peak):
     """Stage times (per kind, and per stage the union of the kinds'
     intervals), counters, truth checks and the roofline of a timed run."""
     from paper_2009_13349_gb300 import ccd
-    batches, marks, stage_sets = S["wl"].batches, S["marks"], S["stage_sets"]
+    batches, marks, stage_sets = S["batches"], S["marks"], S["stage_sets"]
     stage_ms = np.zeros((len(batches), 4))
     span_ms = np.zeros(4)
     for s in range(steps):
@@ -422,23 +458,30 @@ def run_native(args):
     peak = fp64_peak(ccd, sms)
     S = measure_simulation_mixed(args, dev, args.steps, args.warmup,
                                  parallel.rank_seed(args.seed, rank))
-    batches = S["wl"].batches
+    batches, jobs = S["batches"], S["jobs"]
+    in_bytes = 192 * sum(b.n for b in batches)
+    # inputs that fit in L2 are evicted before every step by writing a
+    # buffer twice its size; each step is then timed on its own
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if in_bytes <= 129e6 else None
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = Clocks(local)
     clocks.start()
-    S["marks"][0].record(S["stream"])
     for s in range(args.steps):
+        if flush is not None:
+            flush.fill_(s & 0xFF)
+        S["marks"][s].record(S["stream"])
         S["step"](S["stage_sets"][s])
-        S["marks"][s + 1].record(S["stream"])
+        ends[s].record(S["stream"])
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     marks = S["marks"]
-    step_ms = [marks[s].elapsed_time(marks[s + 1]) for s in range(args.steps)]
-    total_ms = parallel.max_over_ranks(marks[0].elapsed_time(marks[-1]), device=dev)
+    step_ms = [marks[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    total_ms = parallel.max_over_ranks(float(sum(step_ms)), device=dev)
     F = simulation_mixed_figures(args, S, args.steps, peak)
     top = F["top"]
     rec = recorded_traffic("solve_kernel<256> simulation-mixed") if top == 3 else None
@@ -451,9 +494,10 @@ def run_native(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {**workload_config(args),
-                   "l2": (f"inputs {192 * args.n / 1e6:.0f} MB per step "
-                          + ("> 129 MB L2; no flush" if 192 * args.n > 129e6
-                             else "< 129 MB L2 (a small case, not a bench value)")),
+                   "l2": (f"inputs {in_bytes / 1e6:.0f} MB per step "
+                          + ("> 129 MB L2; no flush" if flush is None
+                             else "< 129 MB L2: a 256 MB buffer written before each step, "
+                                  "steps timed one by one")),
                    "streams": "the VF and EE batches of a step on two CUDA streams",
                    "parallelism": f"{world} GPU(s), queries sharded, no collective"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -467,12 +511,11 @@ def run_native(args):
                      "duration": "per step, the union of the VF and EE launches' intervals "
                                  "(two streams)",
                      "naive_equivalent_gops": F["naive"] / 1e9},
-        "stage_ms_per_step": {("VF" if b.kind == 0 else "EE"): {STAGES[k]: float(F["stage_ms"][j, k])
-                                                               for k in range(4)}
-                              for j, b in enumerate(batches)},
+        "stage_ms_per_step": {job_label(b, ms): {STAGES[k]: float(F["stage_ms"][j, k])
+                                                 for k in range(4)}
+                              for j, (b, ms) in enumerate(jobs)},
         "stage_union_ms_per_step": {STAGES[k]: float(F["span_ms"][k]) for k in range(4)},
-        "counters": {("VF" if b.kind == 0 else "EE"): F["counters"][j]
-                     for j, b in enumerate(batches)},
+        "counters": {job_label(b, ms): F["counters"][j] for j, (b, ms) in enumerate(jobs)},
         "checks": {"mean": float(F["checks"].mean()),
                    "p99": float(np.percentile(F["checks"], 99)), "max": int(F["checks"].max()),
                    "early_termination_pct": float(100.0 * np.mean(F["checks"] >= args.max_itr))},
@@ -489,12 +532,14 @@ def run_native(args):
         dres = [ccd.Result(r.collides, r.toi, r.out_tol, None) for r in S["res"]]
 
         def e2e_step():
-            for j, b in enumerate(batches):
+            for j, (b, ms) in enumerate(jobs):
                 with torch.cuda.stream(S["side"][j]):
                     S["verts"][j].copy_(host[j], non_blocking=True)
-                    err = ccd.err_from_bounds(b.kind, S["verts"][j], stream=S["side"][j])
-                    ccd.batch(b.kind, S["verts"][j], err, delta=1e-6, max_itr=args.max_itr,
-                              ws=S["ws"][j], out=dres[j], stream=S["side"][j])
+                    err = ccd.err_from_bounds(b.kind, S["verts"][j], ms_nonzero=ms > 0,
+                                              stream=S["side"][j])
+                    ccd.batch(b.kind, S["verts"][j], err, ms=ms, delta=1e-6,
+                              max_itr=args.max_itr, ws=S["ws"][j], out=dres[j],
+                              stream=S["side"][j])
                     out_host[j][0].copy_(dres[j].collides, non_blocking=True)
                     out_host[j][1].copy_(dres[j].toi, non_blocking=True)
                     out_host[j][2].copy_(dres[j].out_tol, non_blocking=True)
@@ -512,7 +557,11 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        qps, cores, secs, nq = cpu_baseline(batches, args.cpu_sample, max_itr=args.max_itr)
+        # degenerate-heavy queries average about 0.1 core-second in the oracle
+        sample = args.cpu_sample if args.workload != "degenerate-heavy" else min(args.cpu_sample,
+                                                                                 3000)
+        qps, cores, secs, nq = cpu_baseline(batches, sample, max_itr=args.max_itr,
+                                            ms=[ms for _, ms in jobs])
         out["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores,
                                "kind": "oracle",
                                "sample": f"{nq} random queries of the workload ({secs:.1f} s)"}
@@ -583,7 +632,9 @@ def run_multi_instance(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    if args.no_tune:
+    if args.tuning:
+        tuning, timings = json.loads(args.tuning), None
+    elif args.no_tune:
         tuning, timings = None, None
     else:
         tuning, timings = autotune.get_or_tune(_gpu_name(torch, dev), "multi-instance", measure,

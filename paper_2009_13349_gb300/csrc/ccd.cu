@@ -65,6 +65,7 @@ constexpr int POOL_CAP = 64;          // ... boxes per level per query (default)
 constexpr int POOL_CAP_MAX = 4096;
 constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
                                        // launch takes what the occupancy calculator allows)
+constexpr int POOL_BLOCKS_EE = 20;     // edge-edge: 96 registers without spills (21 would cap it at 80)
 constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
 constexpr int DEEP_BLOCKS_PER_SM = 3;  // ... and resident blocks (queries) per SM (80
                                        // registers without spills) ...
@@ -159,6 +160,23 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// GB300 issues FP64 compares and sign changes on the same scarce FP64 pipe
+// as add and multiply (about two operations per SM per clock), so the
+// per-box tests below take them from the bits instead.
+// x == +-0
+__device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+// -x (the sign bit flipped, as IEEE negation does)
+__device__ __forceinline__ double dneg(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+// t = t_max * s for s = a 2^-k in [0, 1]: the product is s itself when
+// t_max == 1 (the whole-step interval), so the multiply is skipped then
+__device__ __forceinline__ double tscale(double t_max, double s)
+{
+    return __double_as_longlong(t_max) == 0x3FF0000000000000LL ? s : dmul(t_max, s);
+}
+
 // ---- per-query data ---------------------------------------------------------
 
 struct Query {
@@ -194,8 +212,8 @@ __device__ __forceinline__ double dkey_inv(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
 // thresholds: x <= c  <=>  dkey(x) <= key_le(c);  x >= c  <=>  dkey(x) >= key_ge(c)
-__device__ __forceinline__ long long key_le(double c) { return c == 0.0 ? 0LL : dkey(c); }
-__device__ __forceinline__ long long key_ge(double c) { return c == 0.0 ? -1LL : dkey(c); }
+__device__ __forceinline__ long long key_le(double c) { return dzero(c) ? 0LL : dkey(c); }
+__device__ __forceinline__ long long key_ge(double c) { return dzero(c) ? -1LL : dkey(c); }
 
 struct Thresholds {
     long long le_eps[3];   // x <= eps_c
@@ -209,7 +227,7 @@ __device__ __forceinline__ void make_thresholds(const double (&eps)[3], double d
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T.le_eps[c] = key_le(eps[c]);
-        T.ge_neps[c] = key_ge(-eps[c]);
+        T.ge_neps[c] = key_ge(dneg(eps[c]));
     }
     T.delta = dkey(delta);
 }
@@ -329,7 +347,7 @@ __device__ __forceinline__ void box_test_keys(const long long (&km)[3], const lo
         const double wc = dsub(M, m);           // >= +0
         const long long kc = __double_as_longlong(wc);
         if (c == 0 || kc > kw) { kw = kc; wmax = wc; }
-        if (ms != 0.0) {
+        if (!dzero(ms)) {
             lo[c] = dkey(dsub(m, ms));
             hi[c] = dkey(dadd(M, ms));
         } else {
@@ -840,7 +858,7 @@ __device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
         tqs += (unsigned long long)ntv;
         for (int task = tid; task < 3 * ntv; task += BS) {
             const int tv = task / 3;
-            t_quantities_axis<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[tv], k[0])), task - 3 * tv,
+            t_quantities_axis<KIND>(Q, tscale(q.t_max, dyadic(s.run_at[tv], k[0])), task - 3 * tv,
                                     sh.tq[tv]);
         }
     }
@@ -1144,7 +1162,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
             bsync<BS>();
             tqs += 2 * (unsigned long long)nrun;
             for (int task = tid; task < 2 * nrun; task += BS)
-                t_quantities<KIND>(Q, dmul(q.t_max, dyadic(s.run_at[task >> 1] + (task & 1), k[0])),
+                t_quantities<KIND>(Q, tscale(q.t_max, dyadic(s.run_at[task >> 1] + (task & 1), k[0])),
                                    tq + task * W);
             bsync<BS>();
             if (valid) {
@@ -1461,10 +1479,10 @@ __device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
 // the run ends).  A level with more children than the slot capacity hands the
 // query to the one-warp solver, which restarts it.
 struct PoolSlot {
-    long long qi, size, pos, n_before;
+    long long qi, n_before;
     unsigned long long if_at, pend_at;
-    double first_w;
-    int k[3], sd, can_split, found, nn, np, buf;
+    int size, pos, nn, np;                       // at most pool_cap (<= 4096)
+    unsigned char k[3], sd, can_split, found, buf, pad;
 };
 
 // A slot's query record lives in global memory (one per slot of the
@@ -1478,15 +1496,15 @@ struct PoolMeta {
 
 // What a slot's lanes decided in one iteration, for the slot's owner lane.
 struct PoolAgg {
-    int outcome;                  // 0 continue, 1 answered, 2 handed over
-    int fh;                       // a colliding box in the iteration (0 / 1)
-    int runs;                     // t split: runs of equal t_L that start here
-    int cnt0, cntk;               // t split: colliding boxes of the first / last run
-    int hits;                     // colliding boxes
-    int children;                 // u / v split: children written
     unsigned long long at_fh;     // t_L numerator of the first colliding box
     unsigned long long at_k;      // ... of the last run
-    double w_fh;
+    unsigned char outcome;        // 0 continue, 1 answered, 2 handed over
+    unsigned char fh;             // a colliding box in the iteration (0 / 1)
+    unsigned char runs;           // t split: runs of equal t_L that start here
+    unsigned char cnt0, cntk;     // t split: colliding boxes of the first / last run
+    unsigned char hits;           // colliding boxes
+    unsigned char children;       // u / v split: children written
+    unsigned char pad;
 };
 
 template <int KIND>
@@ -1516,7 +1534,7 @@ __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[
 // segment table (segs != nullptr) each query takes its tolerances from its
 // segment and queries of the other kind are skipped (one launch per kind).
 template <int KIND>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOCKS_EE)
     pool_kernel(Params p, Box *mem, PoolMeta *metas, int cap, const int *list, const int *count_p,
                 int *head, const ccd_segment *segs, int nseg)
 {
@@ -1582,7 +1600,7 @@ __global__ void __launch_bounds__(32)
         // 2. place the slots' next boxes in the lanes, rotating the priority:
         // slot s takes lanes [E_s, E_s + take_s); a lane finds its slot from
         // the mask of segment starts
-        const int rem = active ? (int)min(S.size - S.pos, 32LL) : 0;
+        const int rem = active ? min(S.size - S.pos, 32) : 0;
         const int rrem = __shfl_sync(FULL, rem, (lane + rot) & 31);
         int inc = rrem;
 #pragma unroll
@@ -1649,7 +1667,7 @@ __global__ void __launch_bounds__(32)
         for (int task = lane; task < 3 * ntv; task += 32) {
             const int tv = task / 3;
             const int s2 = sh.tv_slot[tv];
-            t_quantities_axis<KIND>(meta[s2].Q, dmul(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
+            t_quantities_axis<KIND>(meta[s2].Q, tscale(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
                                     task - 3 * tv, sh.tq[tv]);
         }
         __syncwarp();
@@ -1703,7 +1721,6 @@ __global__ void __launch_bounds__(32)
         const int A = As ? __ffs(As) - 1 : 32, O = Os ? __ffs(Os) - 1 : 32;
         const int outcome = (A < 32 && A <= O) ? 1 : (O < 32 ? 2 : 0);
         const unsigned long long at_fh = __shfl_sync(FULL, at, fh < 0 ? lane : fh);
-        const double w_fh = __shfl_sync(FULL, bt.w, fh < 0 ? lane : fh);
         // t split: runs of equal t_L among the slot's colliding boxes; the
         // first may continue the run left open by the previous iteration
         const unsigned hb = Hs & ((1u << lane) - 1u);             // colliding boxes before me
@@ -1723,7 +1740,6 @@ __global__ void __launch_bounds__(32)
             G.outcome = outcome;
             G.fh = fh >= 0;
             G.at_fh = at_fh;
-            G.w_fh = w_fh;
             G.hits = __popc(Hs);
             G.children = incl;
             G.runs = __popc(Rs);
@@ -1780,7 +1796,6 @@ __global__ void __launch_bounds__(32)
             if (!S.found && G.fh && G.outcome != 2) {
                 S.found = 1;
                 S.if_at = G.at_fh;
-                S.first_w = G.w_fh;
             }
             if (G.outcome == 1) {
                 S.qi = -1;
