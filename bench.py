@@ -205,8 +205,13 @@ def stage_ops(c: dict, stage: int, n_by_kind: dict) -> tuple[float, float]:
         ops = sum(n * OPS_PER_CHECK[k] for k, n in n_by_kind.items())
         return ops, ops
     if stage == 1:
+        # boxes from shared partials: SHARED_BOX_OPS each plus the partials;
+        # the rest (iterations with more distinct partials than the table
+        # holds) evaluate their corners directly
         ee, tee = c["evals_pool_ee"], c["tq_pool_ee"]
-        ops = ((c["evals_pool"] - ee) * BOX_OPS[0] + ee * BOX_OPS[1]
+        sh, shee, aee = c["evals_pool_shared"], c["evals_pool_shared_ee"], c["a_tasks_pool_ee"]
+        ops = ((c["evals_pool"] - ee - (sh - shee)) * BOX_OPS[0] + (ee - shee) * BOX_OPS[1]
+               + sh * SHARED_BOX_OPS + (c["a_tasks_pool"] - aee) * A_OPS[0] + aee * A_OPS[1]
                + (c["tq_pool"] - tee) * T_OPS[0] + tee * T_OPS[1])
         return ops, c["checks_pool"] * max(OPS_PER_CHECK.values())
     if stage == 2:

@@ -187,10 +187,14 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * solver (one per distinct t value of an iteration, shared by that
  * iteration's boxes), [24] their edge-edge part, [25] iterations of the
  * pooled solver's warps and [26] the sum over them of the most boxes one
- * query placed in the iteration.  The small-frontier solver of [3], [5], [8]
- * is the one-warp solver.
+ * query placed in the iteration, [27] shared partials computed by the
+ * pooled solver (one per distinct t value and parameter value of an
+ * iteration), [28] their edge-edge part, [29] pooled box evaluations that
+ * used them (the rest evaluated their corners directly) and [30] the
+ * edge-edge part of [29].  The small-frontier solver of [3], [5], [8] is
+ * the one-warp solver.
  */
-#define CCD_NUM_COUNTERS 27
+#define CCD_NUM_COUNTERS 31
 ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int32_t count,
                                   void *stream);
 
@@ -239,7 +243,8 @@ typedef struct {
  *  pool_cap             boxes per level a query may reach in the pooled
  *                       solver before the one-warp solver takes it over,
  *                       32..4096 (64); the pooled slots take
- *                       72 * pool_cap bytes each, 256 slots per SM
+ *                       72 * pool_cap bytes each, 32 slots per pooled
+ *                       block and up to 24 blocks per SM
  */
 typedef struct {
     int32_t deep_threads;

@@ -63,6 +63,7 @@ constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
 constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
 constexpr int POOL_CAP_MAX = 4096;
+constexpr int POOL_PCAP = 64;         // shared partials per pooled iteration (more: direct)
 constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
                                        // launch takes what the occupancy calculator allows)
 constexpr int POOL_BLOCKS_EE = 20;     // edge-edge: 96 registers without spills (21 would cap it at 80)
@@ -115,9 +116,13 @@ struct Header {
     unsigned long long pool_serial; // sum over those of the most boxes one slot placed
     int overflow_ee;  // segmented batches: edge-edge queries in the deep list ...
     int head_deep_ee; // ... and their work counter (vertex-face: overflow, head_deep)
-    int pad[6];
+    unsigned long long a_tasks_pool;          // shared partials computed by the pooled solver
+    unsigned long long a_tasks_pool_ee;       // the part of a_tasks_pool spent on edge-edge queries
+    unsigned long long evals_pool_shared;     // pooled box evaluations from shared partials
+    unsigned long long evals_pool_shared_ee;  // the part of those on edge-edge queries
+    unsigned long long pad[7];
 };
-static_assert(sizeof(Header) == 256, "header is one 256-byte line");
+static_assert(sizeof(Header) == 320, "header is five 64-byte lines");
 
 struct Layout {
     size_t off_surv, off_mid, off_over, off_level, off_dlist, off_jlist, off_kappa, off_pool,
@@ -147,34 +152,68 @@ __device__ __forceinline__ double pow2neg(int k)
     return __longlong_as_double((long long)((unsigned long long)(1023 - k) << 52));
 }
 
-__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
-// 2^-k x, exact: by exponent arithmetic while the result stays normal
-__device__ __forceinline__ double scale2neg(double x, int k)
+// GB300 issues FP64 compares and sign changes on the same scarce FP64 pipe
+// as add and multiply (about two operations per SM per clock), so the
+// per-box tests take them from the bits instead.  The bits pass through a
+// one-instruction move that the compiler cannot see through; a plain
+// reinterpretation lets it turn integer tests of the bits back into
+// floating-point compares.
+__device__ __forceinline__ long long dbits(double x)
 {
-    const long long b = __double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    return (e > k && e < 0x7ff) ? __longlong_as_double(b - ((long long)k << 52))
-                                : __dmul_rn(pow2neg(k), x);
+    long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+    return b;
 }
+__device__ __forceinline__ double dfrombits(long long b)
+{
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(b));
+    return x;
+}
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// GB300 issues FP64 compares and sign changes on the same scarce FP64 pipe
-// as add and multiply (about two operations per SM per clock), so the
-// per-box tests below take them from the bits instead.
+// 2^-k x when the result is not normal (or x is not finite): one rounded
+// multiply, out of line so that the common case never issues it
+__device__ __noinline__ double scale2neg_slow(double x, int k) { return dmul(pow2neg(k), x); }
+// 2^-k x, exact: by exponent arithmetic while the result stays normal
+__device__ __forceinline__ double scale2neg(double x, int k)
+{
+    const long long b = dbits(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e > k && e < 0x7ff) return dfrombits(b - ((long long)k << 52));
+    return scale2neg_slow(x, k);
+}
+
 // x == +-0
-__device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool dzero(double x) { return (dbits(x) << 1) == 0; }
 // -x (the sign bit flipped, as IEEE negation does)
 __device__ __forceinline__ double dneg(double x)
 {
-    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+    return dfrombits(dbits(x) ^ (long long)0x8000000000000000ULL);
 }
 // t = t_max * s for s = a 2^-k in [0, 1]: the product is s itself when
 // t_max == 1 (the whole-step interval), so the multiply is skipped then
+__device__ __forceinline__ bool tmax_one(double t_max) { return dbits(t_max) == 0x3FF0000000000000LL; }
 __device__ __forceinline__ double tscale(double t_max, double s)
 {
-    return __double_as_longlong(t_max) == 0x3FF0000000000000LL ? s : dmul(t_max, s);
+    return tmax_one(t_max) ? s : dmul(t_max, s);
+}
+
+// The split dimension of Algorithm 2: the largest of c_d = 2^-k_d kappa_d,
+// ties to t, then u, then v.  The c_d are +0, positive or +inf (kappa is a
+// maximum of absolute values), where the order of the bits as signed
+// integers is the numeric order.
+__device__ __forceinline__ int split_dim(double ct, double cu, double cv)
+{
+    const long long bt = dbits(ct), bu = dbits(cu), bv = dbits(cv);
+    long long bm = bt;
+    if (bu > bm) bm = bu;
+    if (bv > bm) bm = bv;
+    return (bt == bm) ? 0 : (bu == bm) ? 1 : 2;
 }
 
 // ---- per-query data ---------------------------------------------------------
@@ -204,12 +243,12 @@ __device__ __forceinline__ void load_query(const double *__restrict__ verts, lon
 // the thresholds below absorb).
 __device__ __forceinline__ long long dkey(double x)
 {
-    const long long b = __double_as_longlong(x);
+    const long long b = dbits(x);
     return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 __device__ __forceinline__ double dkey_inv(long long k)
 {
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+    return dfrombits(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
 // thresholds: x <= c  <=>  dkey(x) <= key_le(c);  x >= c  <=>  dkey(x) >= key_ge(c)
 __device__ __forceinline__ long long key_le(double c) { return dzero(c) ? 0LL : dkey(c); }
@@ -299,7 +338,7 @@ __device__ __forceinline__ void corner_range(double y_lo, double y_hi, double g,
     const bool sw = dkey(p1) < dkey(p0);
     const double pmin = sw ? p1 : p0, pmax = sw ? p0 : p1;
     // x g smallest: x_lo = (NEG ? -y_hi : y_lo) when g's sign bit is clear
-    const bool hi_y = (__double_as_longlong(g) < 0) != NEG;
+    const bool hi_y = (dbits(g) < 0) != NEG;
     const double ymin = hi_y ? y_hi : y_lo, ymax = hi_y ? y_lo : y_hi;
     lo = dkey(dfma(NEG ? -ymin : ymin, g, pmin));
     hi = dkey(dfma(NEG ? -ymax : ymax, g, pmax));
@@ -345,7 +384,7 @@ __device__ __forceinline__ void box_test_keys(const long long (&km)[3], const lo
     for (int c = 0; c < 3; ++c) {
         const double m = dkey_inv(km[c]), M = dkey_inv(kM[c]);
         const double wc = dsub(M, m);           // >= +0
-        const long long kc = __double_as_longlong(wc);
+        const long long kc = dbits(wc);
         if (c == 0 || kc > kw) { kw = kc; wmax = wc; }
         if (!dzero(ms)) {
             lo[c] = dkey(dsub(m, ms));
@@ -1112,13 +1151,8 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
 
     for (;;) {
         // split(): c_d = w(I_d) kappa_d, ties t > u > v.  Same for the level.
-        const double ct = scale2neg(kap[0], k[0]);
-        const double cu = scale2neg(kap[1], k[1]);
-        const double cv = scale2neg(kap[2], k[2]);
-        double cm = ct;
-        if (cu > cm) cm = cu;
-        if (cv > cm) cm = cv;
-        const int sd = (ct == cm) ? 0 : (cu == cm) ? 1 : 2;
+        const int sd = split_dim(scale2neg(kap[0], k[0]), scale2neg(kap[1], k[1]),
+                                 scale2neg(kap[2], k[2]));
         // (the deep solver uses selects where the one-warp solver indexes by sd: a
         // dynamic index there puts k and the child boxes in local memory, which
         // kept the VF deep solver from three blocks per SM)
@@ -1482,7 +1516,7 @@ struct PoolSlot {
     long long qi, n_before;
     unsigned long long if_at, pend_at;
     int size, pos, nn, np;                       // at most pool_cap (<= 4096)
-    unsigned char k[3], sd, can_split, found, buf, pad;
+    unsigned char k[3], sd, can_split, found, buf, t_one;   // t_one: t_max == 1
 };
 
 // A slot's query record lives in global memory (one per slot of the
@@ -1516,17 +1550,16 @@ struct PoolShared {
     double tq[64][TWidth<KIND>::W];
     unsigned long long tv_a[64];
     int tv_slot[64];
+    // distinct partials of an iteration: key (t value id << 56 | endpoint
+    // numerator) and value per axis
+    unsigned long long pk[POOL_PCAP];
+    double part[POOL_PCAP][3];
 };
 
 __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[3])
 {
-    const double ct = scale2neg(kap[0], S.k[0]);
-    const double cu = scale2neg(kap[1], S.k[1]);
-    const double cv = scale2neg(kap[2], S.k[2]);
-    double cm = ct;
-    if (cu > cm) cm = cu;
-    if (cv > cm) cm = cv;
-    S.sd = (ct == cm) ? 0 : (cu == cm) ? 1 : 2;
+    S.sd = split_dim(scale2neg(kap[0], S.k[0]), scale2neg(kap[1], S.k[1]),
+                     scale2neg(kap[2], S.k[2]));
     S.can_split = S.k[S.sd] < KMAX;
 }
 
@@ -1547,6 +1580,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
     const int count = *(volatile const int *)count_p;
     bool drained = false;
     unsigned long long evals = 0, checks_done = 0, tqs = 0, iters = 0, serial = 0;
+    unsigned long long ptasks = 0, shared_evals = 0;
     int rot = 0;
     S.qi = -1;
     __syncwarp();
@@ -1586,6 +1620,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
                     S.nn = S.np = 0;
                     S.buf = 0;
                     S.k[0] = S.k[1] = S.k[2] = 0;
+                    S.t_one = tmax_one(meta[lane].qp.t_max);
                     pool_split_dim(S, meta[lane].kap);
                     mine[0] = Box{{0ull, 0ull, 0ull}};
                 } else if (idx >= count) {
@@ -1664,18 +1699,101 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
         if (start) { sh.tv_slot[tl] = so; sh.tv_a[tl] = at; }
         if (open_r) { sh.tv_slot[tl + 1] = so; sh.tv_a[tl + 1] = at + 1; }
         __syncwarp();
-        for (int task = lane; task < 3 * ntv; task += 32) {
-            const int tv = task / 3;
-            const int s2 = sh.tv_slot[tv];
-            t_quantities_axis<KIND>(meta[s2].Q, tscale(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
-                                    task - 3 * tv, sh.tq[tv]);
+        // t = t_max s, where t_max == 1 (the whole step) needs no multiply: a
+        // warp-uniform branch, so that the multiply is not issued at all
+        if (__all_sync(FULL, S.qi < 0 || S.t_one)) {
+            for (int task = lane; task < 3 * ntv; task += 32) {
+                const int tv = task / 3;
+                const int s2 = sh.tv_slot[tv];
+                t_quantities_axis<KIND>(meta[s2].Q, dyadic(sh.tv_a[tv], sh.st[s2].k[0]),
+                                        task - 3 * tv, sh.tq[tv]);
+            }
+        } else {
+            for (int task = lane; task < 3 * ntv; task += 32) {
+                const int tv = task / 3;
+                const int s2 = sh.tv_slot[tv];
+                t_quantities_axis<KIND>(meta[s2].Q,
+                                        dmul(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
+                                        task - 3 * tv, sh.tq[tv]);
+            }
         }
-        __syncwarp();
+        __syncwarp();                  // the t-quantities, for every lane
+        // Partials shared by the iteration's boxes, per axis: VF a(t, u) =
+        // fma(-u, e1, q), EE c(t, v) = p1 - fma(v, d2, p3), keyed by (t value
+        // id, endpoint numerator; a slot's boxes share one level, so one k).
+        // A box needs four: its two t values times its two endpoints.  Of
+        // {tl, tl + 1} one is even and one odd, and so are the endpoints a and
+        // a + 1, so each of a box's keys has its own class (t parity, endpoint
+        // parity) and equal keys always meet in the same class: one match per
+        // class finds every repeat.  The distinct partials are computed once
+        // each, as a dense task list, and the boxes read them from shared
+        // memory (the same fused operations as evaluating the corners
+        // directly, so the same bits).
+        constexpr int PD = KIND == CCD_KIND_VF ? 1 : 2;   // the partial's parameter
+        constexpr int FD = 3 - PD;                        // the fused one
+        const unsigned hmask = __ballot_sync(FULL, have);
+        const unsigned long long e0 = b.a[PD];
+        const int pt = tl & 1, pe = (int)(e0 & 1);
+        int pid[4];       // id of this box's key of class (t parity << 1 | endpoint parity)
+        int np = 0;
+#pragma unroll
+        for (int cls = 0; cls < 4; ++cls) {
+            const int tv = ((cls >> 1) == pt) ? tl : tl + 1;
+            const unsigned long long key =
+                ((unsigned long long)tv << 56) | (((cls & 1) == pe) ? e0 : e0 + 1);
+            unsigned m = 0;
+            if (have) m = __match_any_sync(hmask, key);
+            const int lead = have ? __ffs(m) - 1 : lane;
+            const unsigned L = __ballot_sync(FULL, have && lead == lane);
+            pid[cls] = np + __popc(L & ((1u << lead) - 1u));
+            if (have && lead == lane && pid[cls] < POOL_PCAP) sh.pk[pid[cls]] = key;
+            np += __popc(L);
+        }
+        const bool shared_p = np <= POOL_PCAP;           // warp-uniform
+        if (shared_p) {
+            ptasks += (unsigned long long)np;             // warp-uniform tally
+            shared_evals += (unsigned long long)nbox;
+            __syncwarp();              // the keys
+            for (int task = lane; task < np; task += 32) {
+                const unsigned long long key = sh.pk[task];
+                const int tv = (int)(key >> 56);
+                const double x = dyadic(key & ((1ull << 56) - 1), sh.st[sh.tv_slot[tv]].k[PD]);
+                const double *Tq = sh.tq[tv];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    sh.part[task][c] = KIND == CCD_KIND_VF
+                                           ? dfma(-x, Tq[3 + c], Tq[c])
+                                           : dsub(Tq[c], dfma(x, Tq[9 + c], Tq[6 + c]));
+            }
+            __syncwarp();
+        }
         if (have) {
             long long km[3], kM[3];
-            corners_keys<KIND>(sh.tq[tl], sh.tq[tl + 1], dyadic(b.a[1], T.k[1]),
-                               dyadic(b.a[1] + 1, T.k[1]), dyadic(b.a[2], T.k[2]),
-                               dyadic(b.a[2] + 1, T.k[2]), km, kM);
+            if (shared_p) {
+                const double yl = dyadic(b.a[FD], T.k[FD]), yr = dyadic(b.a[FD] + 1, T.k[FD]);
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    // classes of (tl + side, a) and (tl + side, a + 1)
+                    const int c0 = ((pt ^ side) << 1) | pe, c1 = c0 ^ 1;
+                    const int i0 = c0 == 0 ? pid[0] : c0 == 1 ? pid[1] : c0 == 2 ? pid[2] : pid[3];
+                    const int i1 = c1 == 0 ? pid[0] : c1 == 1 ? pid[1] : c1 == 2 ? pid[2] : pid[3];
+                    const double *Tq = sh.tq[tl + side];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        // VF: fma(-v, e2, a); EE: fma(u, d1, c)
+                        const double g = KIND == CCD_KIND_VF ? Tq[6 + c] : Tq[3 + c];
+                        long long lo, hi;
+                        corner_range<KIND == CCD_KIND_VF>(yl, yr, g, sh.part[i0][c],
+                                                          sh.part[i1][c], lo, hi);
+                        if (side == 0) { km[c] = lo; kM[c] = hi; }
+                        else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
+                    }
+                }
+            } else {
+                corners_keys<KIND>(sh.tq[tl], sh.tq[tl + 1], dyadic(b.a[1], T.k[1]),
+                                   dyadic(b.a[1] + 1, T.k[1]), dyadic(b.a[2], T.k[2]),
+                                   dyadic(b.a[2] + 1, T.k[2]), km, kM);
+            }
             Thresholds TH;   // a few integer operations: cheaper than keeping 32 in shared memory
             make_thresholds(meta[so].qp.eps, meta[so].qp.delta, TH);
             box_test_keys(km, kM, TH, meta[so].qp.ms, bt.hit, bt.term, bt.w);
@@ -1848,6 +1966,12 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
         if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->tq_pool_ee, tqs);
         atomicAdd(&p.hdr->pool_iters, iters);
         atomicAdd(&p.hdr->pool_serial, serial);
+        atomicAdd(&p.hdr->a_tasks_pool, ptasks);
+        atomicAdd(&p.hdr->evals_pool_shared, shared_evals);
+        if (KIND == CCD_KIND_EE) {
+            atomicAdd(&p.hdr->a_tasks_pool_ee, ptasks);
+            atomicAdd(&p.hdr->evals_pool_shared_ee, shared_evals);
+        }
     }
     atomicAdd(&p.hdr->checks_pool, checks_done);
 }
@@ -2717,7 +2841,8 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int3
         (int64_t)h.tq_deep_ee, (int64_t)h.a_tasks_deep_ee, (int64_t)h.evals_pool_ee,
         (int64_t)h.tq_small_ee, (int64_t)h.evals_small_ee, h.jumbo, h.pages_peak,
         (int64_t)h.tq_pool, (int64_t)h.tq_pool_ee, (int64_t)h.pool_iters,
-        (int64_t)h.pool_serial};
+        (int64_t)h.pool_serial, (int64_t)h.a_tasks_pool, (int64_t)h.a_tasks_pool_ee,
+        (int64_t)h.evals_pool_shared, (int64_t)h.evals_pool_shared_ee};
     for (int i = 0; i < count && i < CCD_NUM_COUNTERS; ++i) counters[i] = all[i];
     return CCD_OK;
 }

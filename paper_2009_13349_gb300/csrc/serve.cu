@@ -394,7 +394,7 @@ ccd_status ccd_batch_begin(const ccd_server_config *config, ccd_server **out)
         L.b.workspace = b;
         L.b.ws_bytes = al256(served_workspace_bytes(c.max_batch, c.max_itr_bound));
         void *h = nullptr;
-        const size_t hb = al256(n) + 3 * al256(8 * n) + 256;
+        const size_t hb = al256(n) + 3 * al256(8 * n) + al256(header_bytes());
         if (cudaHostAlloc(&h, hb, cudaHostAllocDefault) != cudaSuccess) { destroy(S); return CCD_ERR_CUDA; }
         char *hc = (char *)h;
         L.h_col = (uint8_t *)hc; hc += al256(n);
