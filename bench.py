@@ -177,9 +177,9 @@ class Clocks:
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu record
-    (profiles/traffic.json, written by a capture of the current source), or
-    None if there is none or the kernel source changed since."""
+    """The committed ncu record of ``kernel``'s DRAM traffic
+    (profiles/traffic.json, from a small-case capture of the current
+    source), or None if there is none or the kernel source changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2009_13349_gb300", "csrc", "ccd.cu")
@@ -191,6 +191,20 @@ def recorded_traffic(kernel: str):
     if not rec or rec.get("sha256_prefix") != sha:
         return None
     return rec
+
+
+def stage_traffic(kernel: str, c: dict, stage: int):
+    """DRAM bytes per step of a solver stage: the recorded bytes per
+    evaluated box of each kind (small-case capture) times this run's boxes,
+    from the kernels' counters.  None without a record of the current
+    source."""
+    rec = recorded_traffic(kernel)
+    if not rec or stage not in (1, 2, 3):
+        return None
+    ev, ee = {1: ("evals_pool", "evals_pool_ee"), 2: ("evals_small", "evals_small_ee"),
+              3: ("evals_deep", "evals_deep_ee")}[stage]
+    bpb = rec["bytes_per_box"]
+    return bpb["0"] * (c[ev] - c[ee]) + bpb["1"] * c[ee]
 
 
 STAGES = ["root_kernel", "pool_kernel (pooled small frontiers)",
@@ -220,10 +234,10 @@ def stage_ops(c: dict, stage: int, n_by_kind: dict) -> tuple[float, float]:
                + (c["evals_small"] - eee) * BOX_OPS[0] + eee * BOX_OPS[1])
         return ops, c["checks_small"] * max(OPS_PER_CHECK.values())
     tee, aee = c["tq_deep_ee"], c["a_tasks_deep_ee"]
-    shared = c["evals_shared_deep"]
+    shared, shee, evee = c["evals_shared_deep"], c["evals_shared_deep_ee"], c["evals_deep_ee"]
     ops = ((c["tq_deep"] - tee) * T_OPS[0] + tee * T_OPS[1] + (c["a_tasks_deep"] - aee) * A_OPS[0]
            + aee * A_OPS[1] + shared * SHARED_BOX_OPS
-           + (c["evals_deep"] - shared) * max(BOX_OPS.values()))
+           + (c["evals_deep"] - evee - (shared - shee)) * BOX_OPS[0] + (evee - shee) * BOX_OPS[1])
     return ops, c["checks_deep"] * max(OPS_PER_CHECK.values())
 
 
@@ -489,7 +503,10 @@ def run_native(args):
     total_ms = parallel.max_over_ranks(float(sum(step_ms)), device=dev)
     F = simulation_mixed_figures(args, S, args.steps, peak)
     top = F["top"]
-    rec = recorded_traffic("solve_kernel<256> simulation-mixed") if top == 3 else None
+    traffic = None
+    if top == 3:
+        traffic = sum(stage_traffic("solve_kernel<256> " + args.workload, c, 3) or 0
+                      for c in F["counters"]) or None
     total_queries = sum(b.n for b in batches) * world
     out = {
         "metric": METRIC, "value": parallel.job_throughput(sum(b.n for b in batches), world,
@@ -509,7 +526,8 @@ def run_native(args):
                        "p99": float(np.percentile(step_ms, 99))},
         "roofline": {"bound": "alu", "kernel": STAGES[top], "achieved": F["achieved"] / 1e9,
                      "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": F["achieved"] / peak,
-                     "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                     "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per step of the stage (all its launches)",
                      "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
                                     "(one FP64 pipe op = one add, mul or fma)",
                      "work": "executed FP64 add/sub/mul/fma instructions from the kernel's counters",
@@ -724,7 +742,8 @@ def run_multi_instance(args):
     kname = ("solve_kernel_seg<256> (deep)" if top == 3 else
              STAGES[top].replace("solve_kernel<32>", "solve_kernel_seg<32>")
              .replace("root_kernel", "root_kernel_seg"))
-    rec = recorded_traffic("solve_kernel_seg<256> multi-instance") if top == 3 else None
+    traffic = stage_traffic({1: "pool_kernel multi-instance",
+                             3: "solve_kernel_seg<256> multi-instance"}.get(top, ""), counters, top)
 
     fn, toi_bad, off = 0, 0, 0
     for b in wl.batches:
@@ -749,7 +768,8 @@ def run_multi_instance(args):
                        "p99": float(np.percentile(step_ms, 99))},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "G FP64 ops/s", "frac": achieved / peak,
-                     "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                     "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per step of the stage (all its launches)",
                      "peak_source": "FP64 fma.rn.f64 issue rate measured in this run "
                                     "(one FP64 pipe op = one add, mul or fma)",
                      "work": "executed FP64 add/sub/mul/fma instructions from the kernel's "

@@ -190,11 +190,11 @@ ccd_status ccd_workspace_status(const void *workspace, int32_t *status,
  * query placed in the iteration, [27] shared partials computed by the
  * pooled solver (one per distinct t value and parameter value of an
  * iteration), [28] their edge-edge part, [29] pooled box evaluations that
- * used them (the rest evaluated their corners directly) and [30] the
- * edge-edge part of [29].  The small-frontier solver of [3], [5], [8] is
- * the one-warp solver.
+ * used them (the rest evaluated their corners directly), [30] the
+ * edge-edge part of [29], [31] the edge-edge part of [6] and [32] of [12].
+ * The small-frontier solver of [3], [5], [8] is the one-warp solver.
  */
-#define CCD_NUM_COUNTERS 31
+#define CCD_NUM_COUNTERS 33
 ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int32_t count,
                                   void *stream);
 

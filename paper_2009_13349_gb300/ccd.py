@@ -241,7 +241,8 @@ COUNTER_NAMES = ("survivors", "deep_queries", "fallbacks", "checks_small", "chec
                  "evals_pool", "tq_deep_ee", "a_tasks_deep_ee", "evals_pool_ee", "tq_small_ee",
                  "evals_small_ee", "deferred_queries", "pages_peak", "tq_pool", "tq_pool_ee",
                  "pool_iters", "pool_serial", "a_tasks_pool", "a_tasks_pool_ee",
-                 "evals_pool_shared", "evals_pool_shared_ee")
+                 "evals_pool_shared", "evals_pool_shared_ee", "evals_deep_ee",
+                 "evals_shared_deep_ee")
 
 
 def workspace_counters(ws: torch.Tensor, stream=None) -> dict:

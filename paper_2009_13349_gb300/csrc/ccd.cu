@@ -120,7 +120,9 @@ struct Header {
     unsigned long long a_tasks_pool_ee;       // the part of a_tasks_pool spent on edge-edge queries
     unsigned long long evals_pool_shared;     // pooled box evaluations from shared partials
     unsigned long long evals_pool_shared_ee;  // the part of those on edge-edge queries
-    unsigned long long pad[7];
+    unsigned long long evals_deep_ee;         // the part of evals_deep on edge-edge queries
+    unsigned long long evals_shared_deep_ee;  // the part of evals_shared_deep on edge-edge queries
+    unsigned long long pad[5];
 };
 static_assert(sizeof(Header) == 320, "header is five 64-byte lines");
 
@@ -775,13 +777,16 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
     atomicAdd(deep ? &p.hdr->tq_deep : &p.hdr->tq_small, tqs);
     if (KIND == CCD_KIND_EE) {
         atomicAdd(deep ? &p.hdr->tq_deep_ee : &p.hdr->tq_small_ee, tqs);
-        if (!deep) atomicAdd(&p.hdr->evals_small_ee, evals);
+        atomicAdd(deep ? &p.hdr->evals_deep_ee : &p.hdr->evals_small_ee, evals);
     }
     if (atasks | split_chunks | shared_evals) {
         atomicAdd(&p.hdr->a_tasks_deep, atasks);
-        if (KIND == CCD_KIND_EE) atomicAdd(&p.hdr->a_tasks_deep_ee, atasks);
         atomicAdd(&p.hdr->split_chunks_deep, split_chunks);
         atomicAdd(&p.hdr->evals_shared_deep, shared_evals);
+        if (KIND == CCD_KIND_EE) {
+            atomicAdd(&p.hdr->a_tasks_deep_ee, atasks);
+            atomicAdd(&p.hdr->evals_shared_deep_ee, shared_evals);
+        }
     }
 }
 
@@ -2842,7 +2847,8 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int3
         (int64_t)h.tq_small_ee, (int64_t)h.evals_small_ee, h.jumbo, h.pages_peak,
         (int64_t)h.tq_pool, (int64_t)h.tq_pool_ee, (int64_t)h.pool_iters,
         (int64_t)h.pool_serial, (int64_t)h.a_tasks_pool, (int64_t)h.a_tasks_pool_ee,
-        (int64_t)h.evals_pool_shared, (int64_t)h.evals_pool_shared_ee};
+        (int64_t)h.evals_pool_shared, (int64_t)h.evals_pool_shared_ee,
+        (int64_t)h.evals_deep_ee, (int64_t)h.evals_shared_deep_ee};
     for (int i = 0; i < count && i < CCD_NUM_COUNTERS; ++i) counters[i] = all[i];
     return CCD_OK;
 }
