@@ -63,7 +63,8 @@ constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
 constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
 constexpr int POOL_CAP_MAX = 4096;
-constexpr int POOL_PCAP = 64;         // shared partials per pooled iteration (more: direct)
+constexpr int POOL_PCAP = 62;         // shared partials per pooled iteration (more: direct;
+                                      // 62 keeps the vertex-face block at 24 per SM)
 constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
                                        // launch takes what the occupancy calculator allows)
 constexpr int POOL_BLOCKS_EE = 20;     // edge-edge: 96 registers without spills (21 would cap it at 80)
@@ -1518,7 +1519,9 @@ __device__ __forceinline__ QP qp_segment(const ccd_segment &sg)
 // the run ends).  A level with more children than the slot capacity hands the
 // query to the one-warp solver, which restarts it.
 struct PoolSlot {
-    long long qi, n_before;
+    int qi;                                      // query index (batches hold < 2^31)
+    int n_before;                                // checks before this level: at most
+                                                 // 3 KMAX levels of pool_cap boxes
     unsigned long long if_at, pend_at;
     int size, pos, nn, np;                       // at most pool_cap (<= 4096)
     unsigned char k[3], sd, can_split, found, buf, t_one;   // t_one: t_max == 1
@@ -1546,19 +1549,26 @@ struct PoolAgg {
     unsigned char pad;
 };
 
+constexpr int TV_SLOT_SHIFT = 58;     // numerators stay below 2^54
+constexpr unsigned long long TV_A_MASK = (1ull << TV_SLOT_SHIFT) - 1;
+
 template <int KIND>
 struct PoolShared {
     PoolSlot st[POOL_SLOTS];
-    PoolAgg agg[POOL_SLOTS];
-    int seg_slot[32];             // slot of the segment of lanes starting at a lane
-    // distinct t values of an iteration (at most 32 runs + 31 gaps + 1)
+    unsigned char seg_slot[32];   // slot of the segment of lanes starting at a lane
+    // distinct t values of an iteration (at most 32 runs + 31 gaps + 1):
+    // t-quantities, and slot << TV_SLOT_SHIFT | t_L numerator
     double tq[64][TWidth<KIND>::W];
     unsigned long long tv_a[64];
-    int tv_slot[64];
-    // distinct partials of an iteration: key (t value id << 56 | endpoint
-    // numerator) and value per axis
-    unsigned long long pk[POOL_PCAP];
-    double part[POOL_PCAP][3];
+    union {
+        // distinct partials of an iteration (box evaluation): key (t value
+        // id << 56 | endpoint numerator) and value per axis
+        struct {
+            unsigned long long pk[POOL_PCAP];
+            double part[POOL_PCAP][3];
+        } sp;
+        PoolAgg agg[POOL_SLOTS];  // the slots' decisions (bookkeeping, after it)
+    };
 };
 
 __device__ __forceinline__ void pool_split_dim(PoolSlot &S, const double (&kap)[3])
@@ -1617,7 +1627,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
                     load_query(p.verts, p.n, qi, meta[lane].Q);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) meta[lane].kap[c] = p.kappa[3 * qi + c];
-                    S.qi = qi;
+                    S.qi = (int)qi;
                     S.size = 1;
                     S.pos = 0;
                     S.n_before = 0;
@@ -1701,24 +1711,26 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
         const int last = __shfl_sync(FULL, pk, 31);
         const int ntv = nbox > 0 ? (last & 0xff) + (last >> 8) + 1 : 0;
         tqs += (unsigned long long)ntv;   // warp-uniform: every lane's tally is the warp's
-        if (start) { sh.tv_slot[tl] = so; sh.tv_a[tl] = at; }
-        if (open_r) { sh.tv_slot[tl + 1] = so; sh.tv_a[tl + 1] = at + 1; }
+        if (start) sh.tv_a[tl] = ((unsigned long long)so << TV_SLOT_SHIFT) | at;
+        if (open_r) sh.tv_a[tl + 1] = ((unsigned long long)so << TV_SLOT_SHIFT) | (at + 1);
         __syncwarp();
         // t = t_max s, where t_max == 1 (the whole step) needs no multiply: a
         // warp-uniform branch, so that the multiply is not issued at all
         if (__all_sync(FULL, S.qi < 0 || S.t_one)) {
             for (int task = lane; task < 3 * ntv; task += 32) {
                 const int tv = task / 3;
-                const int s2 = sh.tv_slot[tv];
-                t_quantities_axis<KIND>(meta[s2].Q, dyadic(sh.tv_a[tv], sh.st[s2].k[0]),
+                const unsigned long long ta = sh.tv_a[tv];
+                const int s2 = (int)(ta >> TV_SLOT_SHIFT);
+                t_quantities_axis<KIND>(meta[s2].Q, dyadic(ta & TV_A_MASK, sh.st[s2].k[0]),
                                         task - 3 * tv, sh.tq[tv]);
             }
         } else {
             for (int task = lane; task < 3 * ntv; task += 32) {
                 const int tv = task / 3;
-                const int s2 = sh.tv_slot[tv];
+                const unsigned long long ta = sh.tv_a[tv];
+                const int s2 = (int)(ta >> TV_SLOT_SHIFT);
                 t_quantities_axis<KIND>(meta[s2].Q,
-                                        dmul(meta[s2].qp.t_max, dyadic(sh.tv_a[tv], sh.st[s2].k[0])),
+                                        dmul(meta[s2].qp.t_max, dyadic(ta & TV_A_MASK, sh.st[s2].k[0])),
                                         task - 3 * tv, sh.tq[tv]);
             }
         }
@@ -1751,7 +1763,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
             const int lead = have ? __ffs(m) - 1 : lane;
             const unsigned L = __ballot_sync(FULL, have && lead == lane);
             pid[cls] = np + __popc(L & ((1u << lead) - 1u));
-            if (have && lead == lane && pid[cls] < POOL_PCAP) sh.pk[pid[cls]] = key;
+            if (have && lead == lane && pid[cls] < POOL_PCAP) sh.sp.pk[pid[cls]] = key;
             np += __popc(L);
         }
         const bool shared_p = np <= POOL_PCAP;           // warp-uniform
@@ -1760,13 +1772,14 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
             shared_evals += (unsigned long long)nbox;
             __syncwarp();              // the keys
             for (int task = lane; task < np; task += 32) {
-                const unsigned long long key = sh.pk[task];
+                const unsigned long long key = sh.sp.pk[task];
                 const int tv = (int)(key >> 56);
-                const double x = dyadic(key & ((1ull << 56) - 1), sh.st[sh.tv_slot[tv]].k[PD]);
+                const double x = dyadic(key & ((1ull << 56) - 1),
+                                        sh.st[(int)(sh.tv_a[tv] >> TV_SLOT_SHIFT)].k[PD]);
                 const double *Tq = sh.tq[tv];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    sh.part[task][c] = KIND == CCD_KIND_VF
+                    sh.sp.part[task][c] = KIND == CCD_KIND_VF
                                            ? dfma(-x, Tq[3 + c], Tq[c])
                                            : dsub(Tq[c], dfma(x, Tq[9 + c], Tq[6 + c]));
             }
@@ -1788,8 +1801,8 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
                         // VF: fma(-v, e2, a); EE: fma(u, d1, c)
                         const double g = KIND == CCD_KIND_VF ? Tq[6 + c] : Tq[3 + c];
                         long long lo, hi;
-                        corner_range<KIND == CCD_KIND_VF>(yl, yr, g, sh.part[i0][c],
-                                                          sh.part[i1][c], lo, hi);
+                        corner_range<KIND == CCD_KIND_VF>(yl, yr, g, sh.sp.part[i0][c],
+                                                          sh.sp.part[i1][c], lo, hi);
                         if (side == 0) { km[c] = lo; kM[c] = hi; }
                         else { km[c] = min(km[c], lo); kM[c] = max(kM[c], hi); }
                     }
@@ -1804,6 +1817,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
             box_test_keys(km, kM, TH, meta[so].qp.ms, bt.hit, bt.term, bt.w);
         }
 
+        __syncwarp();   // the partials are read: their space takes the decisions next
         // 4. Algorithm 2's bookkeeping for every slot at once, with the
         // results of the sequential loop over the slot's boxes in Q order.
         // Box at lane L is check n = n_before + pos + (L - E) + 1.  Ballots
@@ -1816,7 +1830,7 @@ __global__ void __launch_bounds__(32, KIND == 0 ? POOL_BLOCKS_PER_SM : POOL_BLOC
         // prefix count; t splits in runs of equal t_L, all left children of
         // a run, then its right children, where a run still open at the end
         // of the iteration keeps its right children in the pending list.
-        const long long n_L = T.n_before + T.pos + off + 1;
+        const long long n_L = (long long)T.n_before + T.pos + off + 1;
         const bool hit = have && bt.hit;
         const unsigned Hs = __ballot_sync(FULL, hit) & segmask;
         const int fh = Hs ? __ffs(Hs) - 1 : -1;
