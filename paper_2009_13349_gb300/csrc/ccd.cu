@@ -440,19 +440,6 @@ __device__ __forceinline__ void bsync()
     if (BS == 32) __syncwarp(); else __syncthreads();
 }
 
-__device__ __forceinline__ long long warp_minl(long long v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = min(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ long long warp_maxl(long long v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // Per-warp summary of one chunk's box tests, published before one barrier.
 struct WarpDecision {
@@ -475,34 +462,6 @@ struct Smem {
     int ired[BS / 32 + 1];
     long long lred[BS / 32 + 1];
 };
-
-template <int BS>
-__device__ __forceinline__ long long block_minl(long long v, Smem<BS> &s)
-{
-    v = warp_minl(v);
-    if (BS == 32) return v;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s.lred[warp] = v;
-    __syncthreads();
-    long long r = lane < BS / 32 ? s.lred[lane] : BIGL;
-    r = warp_minl(r);
-    __syncthreads();
-    return r;
-}
-
-template <int BS>
-__device__ __forceinline__ long long block_maxl(long long v, Smem<BS> &s)
-{
-    v = warp_maxl(v);
-    if (BS == 32) return v;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s.lred[warp] = v;
-    __syncthreads();
-    long long r = lane < BS / 32 ? s.lred[lane] : -1;
-    r = warp_maxl(r);
-    __syncthreads();
-    return r;
-}
 
 // exclusive prefix sum of v over the block (thread order); *total = sum
 template <int BS>
@@ -563,9 +522,10 @@ __device__ __forceinline__ int block_scan_1sync(int v, int *total, int *arr)
     return before + inc - v;
 }
 
-// inclusive max-scan over thread order (values >= -1)
+// inclusive max-scan over thread order (values >= -1); *all = the block's
+// maximum (the same pass, no further barrier)
 template <int BS>
-__device__ __forceinline__ long long block_incl_maxscan(long long v, Smem<BS> &s)
+__device__ __forceinline__ long long block_incl_maxscan(long long v, Smem<BS> &s, long long *all)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long inc = v;
@@ -574,18 +534,28 @@ __device__ __forceinline__ long long block_incl_maxscan(long long v, Smem<BS> &s
         long long y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc = max(inc, y);
     }
-    if (BS == 32) return inc;
+    if (BS == 32) {
+        *all = __shfl_sync(0xffffffffu, inc, 31);
+        return inc;
+    }
     if (lane == 31) s.lred[warp] = inc;
     __syncthreads();
-    long long prev = -1;
-    for (int w = 0; w < warp; ++w) prev = max(prev, s.lred[w]);
+    long long prev = -1, tot = -1;
+#pragma unroll
+    for (int w = 0; w < BS / 32; ++w) {
+        const long long x = s.lred[w];
+        if (w < warp) prev = max(prev, x);
+        tot = max(tot, x);
+    }
+    *all = tot;
     __syncthreads();
     return max(prev, inc);
 }
 
-// inclusive min-scan over reversed thread order: min over threads >= me
+// inclusive min-scan over reversed thread order: min over threads >= me;
+// *all = the block's minimum
 template <int BS>
-__device__ __forceinline__ long long block_suffix_min(long long v, Smem<BS> &s)
+__device__ __forceinline__ long long block_suffix_min(long long v, Smem<BS> &s, long long *all)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long inc = v;
@@ -594,11 +564,20 @@ __device__ __forceinline__ long long block_suffix_min(long long v, Smem<BS> &s)
         long long y = __shfl_down_sync(0xffffffffu, inc, o);
         if (lane + o < 32) inc = min(inc, y);
     }
-    if (BS == 32) return inc;
+    if (BS == 32) {
+        *all = __shfl_sync(0xffffffffu, inc, 0);
+        return inc;
+    }
     if (lane == 0) s.lred[warp] = inc;
     __syncthreads();
-    long long nxt = BIGL;
-    for (int w = warp + 1; w < BS / 32; ++w) nxt = min(nxt, s.lred[w]);
+    long long nxt = BIGL, tot = BIGL;
+#pragma unroll
+    for (int w = 0; w < BS / 32; ++w) {
+        const long long x = s.lred[w];
+        if (w > warp) nxt = min(nxt, x);
+        tot = min(tot, x);
+    }
+    *all = tot;
     __syncthreads();
     return min(nxt, inc);
 }
@@ -1309,9 +1288,10 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
                         b = F.c(j);
                         if (j == 0 || F.c(j - 1).a[0] != b.a[0]) v = j;
                     }
-                    const long long gs = max(carry, block_incl_maxscan<BS>(v, s));
+                    long long blk;
+                    const long long gs = max(carry, block_incl_maxscan<BS>(v, s, &blk));
                     if (valid) F.x(j + gs) = Box{{2 * b.a[0], b.a[1], b.a[2]}};
-                    carry = max(carry, block_maxl<BS>(v, s));
+                    carry = max(carry, blk);
                 }
                 long long carry_e = ncol;   // end of the open group, scanning backwards
                 const long long last = ((ncol - 1) / BS) * BS;
@@ -1324,9 +1304,10 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
                         b = F.c(j);
                         if (j + 1 == ncol || F.c(j + 1).a[0] != b.a[0]) v = j + 1;
                     }
-                    const long long ge = min(carry_e, block_suffix_min<BS>(v, s));
+                    long long blk;
+                    const long long ge = min(carry_e, block_suffix_min<BS>(v, s, &blk));
                     if (valid) F.x(j + ge) = Box{{2 * b.a[0] + 1, b.a[1], b.a[2]}};
-                    carry_e = min(carry_e, block_minl<BS>(v, s));
+                    carry_e = min(carry_e, blk);
                 }
             }
         } else {
