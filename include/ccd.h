@@ -56,7 +56,7 @@ typedef enum {
  * It holds per-query lists, the small-frontier solvers' slots and the deep
  * tier:
  *  - a pool of frontier pages (32,768 boxes of 24 bytes = 768 KB each)
- *    shared by the deep solver's blocks (three per SM): each level of a deep
+ *    shared by the deep solver's blocks (six per SM): each level of a deep
  *    query takes pages for its children and frees the previous level's, so
  *    memory follows the frontiers actually reached;
  *  - two full-size slots (two arrays of 2 * max_itr + 64 boxes, which no
@@ -64,8 +64,9 @@ typedef enum {
  *    checked before the limit) for queries that found the pool empty; they
  *    restart there.
  * The pool's size therefore changes speed only, never results.
- * ccd_workspace_bytes gives a pool with, per deep block, pages for one level
- * of 2 * max_itr + 64 boxes (at least two pages); ccd_workspace_bytes_pages
+ * ccd_workspace_bytes gives a pool with pages for one level of
+ * 2 * max_itr + 64 boxes (at least two pages) for three deep blocks per SM
+ * (the six share it; levels rarely reach that size); ccd_workspace_bytes_pages
  * one of `pages` pages (>= 2).  A workspace too small for one full-size slot
  * and two pages is used as contiguous slots of fewer boxes, with the
  * capacity fallback described at ccd_vf_batch.  Both return 0 on bad
@@ -236,8 +237,9 @@ typedef struct {
 /*
  * Launch shapes of the solver kernels.  They change speed only: results are
  * identical for every valid tuning.  A zero field takes the default.
- *  deep_threads         threads of a deep-solver block, 256 or 512 (256)
- *  deep_slots           deep-solver blocks per kind (three per SM)
+ *  deep_threads         threads of a deep-solver block, 128, 256 or 512 (256)
+ *  deep_slots           deep-solver blocks per kind (as many as fit at once:
+ *                       six per SM of 128 threads, three of 256, one of 512)
  *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
  *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
  *  pool_cap             boxes per level a query may reach in the pooled

@@ -8,9 +8,10 @@ and workload tag in a JSON file (``$CCD_TUNING_CACHE`` or
 ``~/.cache/ccd_gb300/tuning.json``).
 
 Tunables (see include/ccd.h):
-  deep_threads         block size of the deep solver (256 or 512)
+  deep_threads         block size of the deep solver (128, 256 or 512)
   deep_slots           deep-solver blocks, i.e. queries with large frontiers
-                       solved at once (0 = three per SM)
+                       solved at once (0 = as many as fit: six per SM of 128
+                       threads, three of 256, one of 512)
   small_blocks_per_sm  one-warp solver blocks per SM (its queue width)
   small_cap            frontier depth of a one-warp solver slot in boxes
   pool_cap             boxes per level a query may reach in the pooled solver
@@ -27,7 +28,7 @@ FIELDS = ("deep_threads", "deep_slots", "small_blocks_per_sm", "small_cap", "poo
 
 def candidates(sms: int) -> list[dict]:
     out = []
-    for dt, slots in ((256, 3 * sms), (256, 2 * sms), (512, sms)):
+    for dt, slots in ((128, 6 * sms), (256, 3 * sms), (256, 2 * sms), (512, sms)):
         for sb in (8, 16):
             for cap in (256, 1024):
                 for pc in (64, 256):
@@ -38,8 +39,8 @@ def candidates(sms: int) -> list[dict]:
 
 def validate(t: dict) -> dict:
     t = {k: int(t.get(k, 0)) for k in FIELDS}
-    if t["deep_threads"] not in (0, 256, 512):
-        raise ValueError("deep_threads must be 256 or 512")
+    if t["deep_threads"] not in (0, 128, 256, 512):
+        raise ValueError("deep_threads must be 128, 256 or 512")
     if t["deep_slots"] < 0 or not 0 <= t["small_blocks_per_sm"] <= 32:
         raise ValueError("bad slot or block count")
     if t["small_cap"] and t["small_cap"] < 64:

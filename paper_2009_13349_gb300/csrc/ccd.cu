@@ -68,11 +68,28 @@ constexpr int POOL_PCAP = 62;         // shared partials per pooled iteration (m
 constexpr int POOL_BLOCKS_PER_SM = 24; // ... and at most this many one-warp blocks per SM (the
                                        // launch takes what the occupancy calculator allows)
 constexpr int POOL_BLOCKS_EE = 20;     // edge-edge: 96 registers without spills (21 would cap it at 80)
-constexpr int DEEP_THREADS = 256;     // deep solver: block size ...
-constexpr int DEEP_BLOCKS_PER_SM = 3;  // ... and resident blocks (queries) per SM (80
-                                       // registers without spills) ...
-constexpr int SEG_DEEP_BLOCKS_PER_SM = 2;  // ... and for the segmented kernel, which runs
-                                           // both kinds
+// Resident deep-solver blocks (queries) per SM by block size, at 80
+// registers without spills: one 512-thread block, three of 256, six of 128;
+// a segmented kernel compiled for both kinds needs more registers (two of
+// 256, four of 128).
+constexpr int deep_blocks_per_sm(int bs, bool both_kinds = false)
+{
+    return bs == 256 ? (both_kinds ? 2 : 3) : bs == 128 ? (both_kinds ? 4 : 6) : 1;
+}
+// Single-kind batches run 128-thread deep blocks, six per SM: more queries
+// in flight per SM and barriers over four warps instead of eight (the
+// degenerate-heavy step took 4.71 s against 5.46 s with 256-thread blocks,
+// the simulation-mixed one 93 ms against 103).  Segmented batches default to
+// 256 threads: their few deep queries (about 5,000 of 20M) end in a tail
+// where each query's block width counts more (deep stage 33 vs 47 ms).
+constexpr int DEEP_THREADS = 128;
+constexpr int DEEP_BLOCKS_PER_SM = deep_blocks_per_sm(DEEP_THREADS);
+constexpr int SEG_DEEP_THREADS = 256;
+// The default page pool holds one full-size level for at most this many deep
+// blocks per SM; more blocks share it (pages are taken per level as needed,
+// and a block that finds none defers its query, so the size changes speed
+// only).  Peak use on the degenerate-heavy workload is about a quarter.
+constexpr int DEEP_POOL_BLOCKS_PER_SM = 3;
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
 struct Box {
@@ -786,39 +803,49 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 // ids follow from one block scan (t_L of run r has id r + gaps up to r; t_R
 // has that id + 1).  Distinct keys are found with a shared-memory hash
 // table; dense partial ids come from a second block scan; tasks are packed
-// into consecutive lanes.  A chunk with more than SH_RUN_CAP runs or
-// SH_ENTRY_CAP distinct partials is evaluated as sub-chunks of SH_SUB boxes,
-// which always fit (a box adds at most one run, two t values and four
-// partials); every box gets the same rounded operations either way.
-constexpr int SH_RUN_CAP = 128;
-constexpr int SH_TV_CAP = 2 * SH_RUN_CAP;           // distinct t values per chunk
-constexpr int SH_ENTRY_CAP = 512;                   // partials (one t value each)
-constexpr int SH_SUB = 128;
-static_assert(SH_SUB <= SH_RUN_CAP && 2 * SH_SUB <= SH_TV_CAP && 4 * SH_SUB <= SH_ENTRY_CAP,
-              "a sub-chunk always fits the tables");
-constexpr int SH_SLOTS = 2048;                      // hash slots, power of two
+// into consecutive lanes.  A chunk with more than RUN runs or ENTRY
+// distinct partials is evaluated as sub-chunks of SUB boxes, which always fit
+// (a box adds at most one run, two t values and four partials); every box
+// gets the same rounded operations either way.  The tables scale with the
+// block: 128-thread blocks (six per SM) take half of a 256-thread block's.
+template <int BS>
+struct ShCaps {
+    static constexpr int RUN = BS >= 256 ? 128 : 64;     // runs of equal t_L per chunk
+    static constexpr int TV = 2 * RUN;                   // distinct t values per chunk
+    static constexpr int ENTRY = BS >= 256 ? 512 : 256;  // partials (one t value each)
+    static constexpr int SUB = RUN;
+    static constexpr int SLOTS = BS >= 256 ? 2048 : 1024;   // hash slots, power of two
+    static_assert(SUB <= RUN && 2 * SUB <= TV && 4 * SUB <= ENTRY,
+                  "a sub-chunk always fits the tables");
+    static_assert(4 * BS <= SLOTS, "every insert finds its key or an empty slot");
+};
 constexpr unsigned long long SH_EMPTY = ~0ull;
 constexpr unsigned long long SH_VAL_MASK = (1ull << 54) - 1;
 
+template <int BS>
 struct SharedUV {
-    unsigned long long key[SH_SLOTS];
-    int id[SH_SLOTS];
-    unsigned long long key_by_id[SH_ENTRY_CAP];
-    double part[SH_ENTRY_CAP][3];
-    double tq[SH_TV_CAP][12];
+    unsigned long long key[ShCaps<BS>::SLOTS];
+    int id[ShCaps<BS>::SLOTS];
+    unsigned long long key_by_id[ShCaps<BS>::ENTRY];
+    double part[ShCaps<BS>::ENTRY][3];
+    double tq[ShCaps<BS>::TV][12];
 };
 
+template <int SLOTS>
 __device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long long key,
                                          bool *inserted)
 {
-    // at most 4 * blockDim.x <= SH_SLOTS distinct keys per chunk (half full for
-    // 256 threads), so probing always ends at the key or at an empty slot
-    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 53);
+    // at most 4 * blockDim.x <= SLOTS distinct keys per chunk (half full for
+    // 128- and 256-thread blocks), so probing always ends at the key or at
+    // an empty slot
+    constexpr int SHIFT = SLOTS == 2048 ? 53 : 54;   // the top log2(SLOTS) bits
+    static_assert((1 << (64 - SHIFT)) == SLOTS, "hash range");
+    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> SHIFT);
     for (;;) {
         const unsigned long long old = atomicCAS(&tab[h], SH_EMPTY, key);
         if (old == SH_EMPTY) { *inserted = true; return (int)h; }
         if (old == key) { *inserted = false; return (int)h; }
-        h = (h + 1) & (SH_SLOTS - 1);
+        h = (h + 1) & (SLOTS - 1);
     }
 }
 
@@ -831,17 +858,17 @@ __device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
                                                   const Thresholds &TH, const int (&k)[3],
                                                   bool valid, const Box &b, int v_begin,
                                                   int v_end,
-                                                  Smem<BS> &s, SharedUV &sh, BoxTest &bt,
+                                                  Smem<BS> &s, SharedUV<BS> &sh, BoxTest &bt,
                                                   unsigned long long &tqs,
                                                   unsigned long long &ptasks,
                                                   unsigned long long &shared_evals)
 {
-    static_assert(4 * BS <= SH_SLOTS, "every insert finds its key or an empty slot");
+    using C = ShCaps<BS>;
     constexpr int PD = KIND == CCD_KIND_VF ? 1 : 2;   // the partial's parameter: u or v
     constexpr int FD = 3 - PD;                        // the fused one: v or u
     const int tid = threadIdx.x;
     s.at[tid] = valid ? b.a[0] : ~0ull;
-    for (int j = tid; j < SH_SLOTS; j += BS) sh.key[j] = SH_EMPTY;
+    for (int j = tid; j < C::SLOTS; j += BS) sh.key[j] = SH_EMPTY;
     __syncthreads();
     // runs of equal t_L, and gaps between consecutive runs' t values (a box
     // outside the (sub-)chunk has a_t = ~0 here)
@@ -852,7 +879,7 @@ __device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
     int tot;
     const int pk = block_scan_1sync<BS>((start ? 1 : 0) | ((gap ? 1 : 0) << 16), &tot, s.scan_a);
     const int nrun = tot & 0xffff, ntv = nrun + (tot >> 16) + 1;
-    if (nrun > SH_RUN_CAP) return false;           // block-uniform
+    if (nrun > C::RUN) return false;               // block-uniform
     const int tl = (pk & 0xffff) + (start ? 0 : -1) + (pk >> 16) + (gap ? 1 : 0);   // id of t_L
     if (start) s.run_at[tl] = b.a[0];
     if (open_r) s.run_at[tl + 1] = b.a[0] + 1;     // t_R not shared with the next run
@@ -864,14 +891,14 @@ __device__ __forceinline__ bool eval_chunk_shared(const Query &Q, const QP &q,
         for (int j = 0; j < 4; ++j) {   // j = 2 * side + d
             bool fresh;
             kk[j] = ((unsigned long long)(tl + (j >> 1)) << 54) | (b.a[PD] + (j & 1));
-            sk[j] = sh_insert(sh.key, kk[j], &fresh);
+            sk[j] = sh_insert<C::SLOTS>(sh.key, kk[j], &fresh);
             if (fresh) ins |= 1u << j;
         }
     }
     __syncthreads();
     const int pack = block_scan_1sync<BS>(__popc(ins), &tot, s.scan_b);
     const int NP = tot;
-    const bool share = NP <= SH_ENTRY_CAP;   // block-uniform
+    const bool share = NP <= C::ENTRY;      // block-uniform
     if (share) {
         int ip = pack;
 #pragma unroll
@@ -1160,13 +1187,13 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
                 int h = 0, he = nv;
                 for (;;) {
                     const bool done = eval_chunk_shared<KIND, BS>(
-                        Q, q, TH, k, valid && tid >= h && tid < he, b, h, he, s, *(SharedUV *)tq,
-                        bt, tqs, atasks, shared_evals);
+                        Q, q, TH, k, valid && tid >= h && tid < he, b, h, he, s,
+                        *(SharedUV<BS> *)tq, bt, tqs, atasks, shared_evals);
                     if (done && he >= nv) break;
                     if (done) h = he;
-                    else if (he - h <= SH_SUB) break;   // unreachable: see SH_SUB
+                    else if (he - h <= ShCaps<BS>::SUB) break;   // unreachable: see ShCaps
                     else ++split_chunks;
-                    he = min(nv, h + SH_SUB);
+                    he = min(nv, h + ShCaps<BS>::SUB);
                 }
             } else {
             // Boxes are in Q order, so equal t_L form contiguous runs: the
@@ -1387,7 +1414,7 @@ __device__ bool solve_query(const Params &p, const QP &q, long long qi, FR &F, b
 // PAGED (deep tier): frontier pages come from `pool`; a query that cannot get
 // them goes to out_list (the full-size stage), where it restarts.
 template <int KIND, int BS, bool PAGED = false>
-__global__ void __launch_bounds__(BS, BS == 256 ? DEEP_BLOCKS_PER_SM : 1)
+__global__ void __launch_bounds__(BS, deep_blocks_per_sm(BS))
     solve_kernel(Params p, int deep, Box *slots, long long cap, PagePool pool, const int *list,
                  const int *count, int *head, int *out_list, unsigned char *out_level,
                  int *out_count)
@@ -2037,9 +2064,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 // launches another round for the queries left in the list; no query is
 // interrupted and nothing waits.
 template <int BS, bool PAGED = false, int KS = -1>
-__global__ void __launch_bounds__(BS, BS == 256 ? (KS >= 0 ? DEEP_BLOCKS_PER_SM
-                                                            : SEG_DEEP_BLOCKS_PER_SM)
-                                               : 1)
+__global__ void __launch_bounds__(BS, deep_blocks_per_sm(BS, KS < 0))
     solve_kernel_seg(Params p, const ccd_segment *segs, int nseg, int deep, Box *slots,
                      long long cap, PagePool pool, long long slice_ns = 0,
                      const volatile int *yield = nullptr)
@@ -2537,10 +2562,14 @@ struct DeepLayout {
 
 long long pages_for(long long boxes) { return (boxes + PAGE_BOXES - 1) / PAGE_BOXES; }
 
-// Pages a default workspace provides: for every deep block one level of the
-// largest size any level can reach (2 m_I boxes), and at least two.
+// Pages a default workspace provides: one level of the largest size any
+// level can reach (2 m_I boxes), and at least two, for every deep block up to
+// DEEP_POOL_BLOCKS_PER_SM per SM.
 long long default_pages(long long nb_deep, long long max_itr)
 {
+    const int sms = device_sms();
+    const long long cap_blocks = (long long)DEEP_POOL_BLOCKS_PER_SM * (sms > 0 ? sms : 1);
+    if (nb_deep > cap_blocks) nb_deep = cap_blocks;
     long long per = pages_for(deep_cap(max_itr));
     return nb_deep * (per < 2 ? 2 : per);
 }
@@ -2679,7 +2708,7 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
                                               &h->survivors, &h->head_pool, nullptr, 0);
     stage_mark(2, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<KIND>::W;
-    const size_t tq_deep = sizeof(SharedUV);   // deep tier: shared partials
+    const size_t tq_deep = sizeof(SharedUV<DEEP_THREADS>);   // deep tier: shared partials
     auto *deep_paged = solve_kernel<KIND, DEEP_THREADS, true>;
     auto *deep_contig = solve_kernel<KIND, DEEP_THREADS, false>;
     for (auto *k : {deep_paged, deep_contig})
@@ -2912,15 +2941,19 @@ struct Tuned {
 
 bool resolve_tuning(const ccd_tuning *t, int sms, Tuned *out)
 {
-    Tuned r{DEEP_THREADS, DEEP_BLOCKS_PER_SM * sms, SMALL_BLOCKS_PER_SM, POOL_CAP, SMALL_CAP};
+    Tuned r{SEG_DEEP_THREADS, deep_blocks_per_sm(SEG_DEEP_THREADS) * sms, SMALL_BLOCKS_PER_SM,
+            POOL_CAP, SMALL_CAP};
     if (t) {
-        if (t->deep_threads) r.deep_threads = t->deep_threads;
+        if (t->deep_threads) {   // resident blocks of that size, unless slots are given
+            r.deep_threads = t->deep_threads;
+            r.deep_slots = deep_blocks_per_sm(r.deep_threads) * sms;
+        }
         if (t->deep_slots) r.deep_slots = t->deep_slots;
         if (t->small_blocks_per_sm) r.small_blocks_per_sm = t->small_blocks_per_sm;
         if (t->small_cap) r.small_cap = t->small_cap;
         if (t->pool_cap) r.pool_cap = t->pool_cap;
     }
-    if (r.deep_threads != 256 && r.deep_threads != 512) return false;
+    if (r.deep_threads != 128 && r.deep_threads != 256 && r.deep_threads != 512) return false;
     if (r.deep_slots < 1 || r.small_blocks_per_sm < 1 || r.small_blocks_per_sm > 32 ||
         r.small_cap < 64 || r.pool_cap < 32 || r.pool_cap > POOL_CAP_MAX)
         return false;
@@ -3031,7 +3064,7 @@ ccd_status multi_plan(const double *verts, int64_t n, const ccd_segment *segs, i
 template <int DT>
 ccd_status set_deep_attributes()
 {
-    const size_t tq_deep = sizeof(SharedUV);
+    const size_t tq_deep = sizeof(SharedUV<DT>);
     for (auto *k : {solve_kernel_seg<DT, true>, solve_kernel_seg<DT, false>,
                     solve_kernel_seg<DT, true, CCD_KIND_VF>, solve_kernel_seg<DT, true, CCD_KIND_EE>,
                     solve_kernel_seg<DT, false, CCD_KIND_VF>,
@@ -3049,7 +3082,9 @@ ccd_status multi_front(const MultiPlan &M, bool init_pool, cudaStream_t st)
     const Params &p = M.p;
     if (cudaMemsetAsync(M.ws, 0, sizeof(Header), st) != cudaSuccess) return CCD_ERR_CUDA;
     if (p.n == 0) return CCD_OK;
-    ccd_status r = M.T.deep_threads == 256 ? set_deep_attributes<256>() : set_deep_attributes<512>();
+    ccd_status r = M.T.deep_threads == 128   ? set_deep_attributes<128>()
+                   : M.T.deep_threads == 256 ? set_deep_attributes<256>()
+                                             : set_deep_attributes<512>();
     if (r != CCD_OK) return r;
     seg_validate_kernel<<<(M.nseg + 255) / 256, 256, 0, st>>>(M.segs, M.nseg, p.n, M.bound, p.hdr);
     stage_mark(0, st);
@@ -3083,7 +3118,7 @@ template <int DT>
 void multi_deep_launch(const MultiPlan &M, long long slice_ns, const volatile int *yield,
                        cudaStream_t st)
 {
-    const size_t tq_deep = sizeof(SharedUV);
+    const size_t tq_deep = sizeof(SharedUV<DT>);
     Box *slots = (Box *)(M.ws + M.D.off_slots);
     if (M.D.paged) {
         solve_kernel_seg<DT, true, CCD_KIND_VF><<<M.D.nb_deep, DT, tq_deep, st>>>(
@@ -3105,7 +3140,8 @@ ccd_status multi_deep(const MultiPlan &M, long long slice_ns, const volatile int
     if (slice_ns > 0 &&
         cudaMemsetAsync(&M.p.hdr->round_start, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return CCD_ERR_CUDA;
-    if (M.T.deep_threads == 256) multi_deep_launch<256>(M, slice_ns, yield, st);
+    if (M.T.deep_threads == 128) multi_deep_launch<128>(M, slice_ns, yield, st);
+    else if (M.T.deep_threads == 256) multi_deep_launch<256>(M, slice_ns, yield, st);
     else multi_deep_launch<512>(M, slice_ns, yield, st);
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ERR_CUDA;
 }
@@ -3114,13 +3150,15 @@ ccd_status multi_deep(const MultiPlan &M, long long slice_ns, const volatile int
 ccd_status multi_jumbo(const MultiPlan &M, cudaStream_t st)
 {
     if (M.p.n > 0 && M.D.paged) {
-        const size_t tq_deep = sizeof(SharedUV);
         Box *slots = (Box *)(M.ws + M.D.off_slots);
-        if (M.T.deep_threads == 256)
-            solve_kernel_seg<256, false><<<M.D.nb_jumbo, 256, tq_deep, st>>>(
+        if (M.T.deep_threads == 128)
+            solve_kernel_seg<128, false><<<M.D.nb_jumbo, 128, sizeof(SharedUV<128>), st>>>(
+                M.p, M.segs, M.nseg, 2, slots, M.D.cap_deep, PagePool{});
+        else if (M.T.deep_threads == 256)
+            solve_kernel_seg<256, false><<<M.D.nb_jumbo, 256, sizeof(SharedUV<256>), st>>>(
                 M.p, M.segs, M.nseg, 2, slots, M.D.cap_deep, PagePool{});
         else
-            solve_kernel_seg<512, false><<<M.D.nb_jumbo, 512, tq_deep, st>>>(
+            solve_kernel_seg<512, false><<<M.D.nb_jumbo, 512, sizeof(SharedUV<512>), st>>>(
                 M.p, M.segs, M.nseg, 2, slots, M.D.cap_deep, PagePool{});
     }
     stage_mark(4, st);
@@ -3561,7 +3599,7 @@ extern "C" ccd_status ccd_vf_batch_static(const double *verts, int64_t n, const 
     const long long blocks = (n + ROOT_THREADS - 1) / ROOT_THREADS;
     root_kernel<CCD_KIND_VF><<<(unsigned)blocks, ROOT_THREADS, 0, st>>>(p);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_VF>::W;
-    const size_t tq_deep = sizeof(SharedUV);
+    const size_t tq_deep = sizeof(SharedUV<DEEP_THREADS>);
     if (cudaFuncSetAttribute(solve_kernel<CCD_KIND_VF, DEEP_THREADS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tq_deep) !=
         cudaSuccess)

@@ -89,6 +89,7 @@ def test_results_independent_of_tuning(ccd):
     for t in ({"deep_threads": 256, "deep_slots": 7, "small_blocks_per_sm": 3, "small_cap": 64},
               {"deep_threads": 512, "deep_slots": 2, "small_blocks_per_sm": 32, "small_cap": 4096},
               {"deep_threads": 256, "deep_slots": 300, "small_blocks_per_sm": 8, "small_cap": 256},
+              {"deep_threads": 128, "deep_slots": 900, "small_blocks_per_sm": 8, "small_cap": 64},
               {"pool_cap": 32}, {"pool_cap": 1024, "small_cap": 64}, {"pool_cap": 4096}):
         _eq(_out(ccd.multi_batch(v, sd, 1_000_000, tuning=t)), base)
 
