@@ -79,7 +79,9 @@ constexpr int deep_blocks_per_sm(int bs, bool both_kinds = false)
 // Single-kind batches run 128-thread deep blocks, six per SM: more queries
 // in flight per SM and barriers over four warps instead of eight (the
 // degenerate-heavy step took 4.71 s against 5.46 s with 256-thread blocks,
-// the simulation-mixed one 93 ms against 103).  Segmented batches default to
+// the simulation-mixed one 93 ms against 103; 64-thread blocks, eleven per
+// SM, took 4.66 s and 117 ms: a query's block width shows in the tail of
+// the simulation workload's few deep queries).  Segmented batches default to
 // 256 threads: their few deep queries (about 5,000 of 20M) end in a tail
 // where each query's block width counts more (deep stage 33 vs 47 ms).
 constexpr int DEEP_THREADS = 128;
@@ -810,11 +812,11 @@ __device__ __forceinline__ void count_done(const Params &p, bool deep, long long
 // block: 128-thread blocks (six per SM) take half of a 256-thread block's.
 template <int BS>
 struct ShCaps {
-    static constexpr int RUN = BS >= 256 ? 128 : 64;     // runs of equal t_L per chunk
-    static constexpr int TV = 2 * RUN;                   // distinct t values per chunk
-    static constexpr int ENTRY = BS >= 256 ? 512 : 256;  // partials (one t value each)
+    static constexpr int RUN = BS >= 256 ? 128 : BS / 2;     // runs of equal t_L per chunk
+    static constexpr int TV = 2 * RUN;                       // distinct t values per chunk
+    static constexpr int ENTRY = BS >= 256 ? 512 : 2 * BS;   // partials (one t value each)
     static constexpr int SUB = RUN;
-    static constexpr int SLOTS = BS >= 256 ? 2048 : 1024;   // hash slots, power of two
+    static constexpr int SLOTS = BS >= 256 ? 2048 : 8 * BS;  // hash slots, power of two
     static_assert(SUB <= RUN && 2 * SUB <= TV && 4 * SUB <= ENTRY,
                   "a sub-chunk always fits the tables");
     static_assert(4 * BS <= SLOTS, "every insert finds its key or an empty slot");
@@ -831,6 +833,8 @@ struct SharedUV {
     double tq[ShCaps<BS>::TV][12];
 };
 
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
 template <int SLOTS>
 __device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long long key,
                                          bool *inserted)
@@ -838,7 +842,7 @@ __device__ __forceinline__ int sh_insert(unsigned long long *tab, unsigned long 
     // at most 4 * blockDim.x <= SLOTS distinct keys per chunk (half full for
     // 128- and 256-thread blocks), so probing always ends at the key or at
     // an empty slot
-    constexpr int SHIFT = SLOTS == 2048 ? 53 : 54;   // the top log2(SLOTS) bits
+    constexpr int SHIFT = 64 - ilog2(SLOTS);   // the product's top log2(SLOTS) bits
     static_assert((1 << (64 - SHIFT)) == SLOTS, "hash range");
     unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> SHIFT);
     for (;;) {
