@@ -241,7 +241,7 @@ typedef struct {
  *  deep_slots           deep-solver blocks per kind (as many as fit at once:
  *                       six per SM of 128 threads, three of 256, one of 512)
  *  small_blocks_per_sm  one-warp solver blocks per SM, 1..32 (16)
- *  small_cap            boxes per one-warp solver frontier, >= 64 (1024)
+ *  small_cap            boxes per one-warp solver frontier, >= 64 (256)
  *  pool_cap             boxes per level a query may reach in the pooled
  *                       solver before the one-warp solver takes it over,
  *                       32..4096 (64); the pooled slots take

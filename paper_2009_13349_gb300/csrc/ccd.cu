@@ -59,7 +59,7 @@ constexpr int KMAX = 53;              // deepest dyadic level per dimension
 constexpr int ROOT_THREADS = 256;
 constexpr int SMALL_THREADS = 32;     // one warp per query
 constexpr int SMALL_BLOCKS_PER_SM = 16;
-constexpr long long SMALL_CAP = 1024; // boxes per small-frontier slot
+constexpr long long SMALL_CAP = 256;  // boxes per small-frontier slot
 constexpr int POOL_SLOTS = 32;        // pooled solver: queries held by one warp ...
 constexpr int POOL_CAP = 64;          // ... boxes per level per query (default) ...
 constexpr int POOL_CAP_MAX = 4096;

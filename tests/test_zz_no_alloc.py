@@ -64,7 +64,7 @@ def test_static_scratch_matches_workspace_entry_point_and_oracle(ms, max_itr):
         ref = (r.collides.cpu().numpy(), r.toi.cpu().numpy(), r.out_tol.cpu().numpy(),
                r.checks.cpu().numpy())
         if which == 1 and max_itr == MAX_ITR:
-            # frontiers beyond 1,024 boxes reach ccd_vf_batch's deep tier; the
+            # frontiers beyond 256 boxes reach ccd_vf_batch's deep tier; the
             # static path's one-warp slots hold 256, so they reach its deep tier
             assert ccd.workspace_counters(ws)["deep_queries"] > 0
         for _ in range(2):                                              # two calls in a row
