@@ -208,7 +208,7 @@ def stage_traffic(kernel: str, c: dict, stage: int):
 
 
 STAGES = ["root_kernel", "pool_kernel (pooled small frontiers)",
-          "solve_kernel<32> (one-warp frontier)", "solve_kernel<256> (deep)"]
+          "solve_kernel<32> (one-warp frontier)", "solve_kernel<128> (deep)"]
 
 
 def stage_ops(c: dict, stage: int, n_by_kind: dict) -> tuple[float, float]:
@@ -505,7 +505,7 @@ def run_native(args):
     top = F["top"]
     traffic = None
     if top == 3:
-        traffic = sum(stage_traffic("solve_kernel<256> " + args.workload, c, 3) or 0
+        traffic = sum(stage_traffic("solve_kernel<128> " + args.workload, c, 3) or 0
                       for c in F["counters"]) or None
     total_queries = sum(b.n for b in batches) * world
     out = {
@@ -739,11 +739,12 @@ def run_multi_instance(args):
                  1: sum(c for c, k in zip(counts, kinds) if k == 1)}
     ops, naive = stage_ops(counters, top, n_by_kind)
     achieved = ops / (mean_stage[top] * 1e-3)
-    kname = ("solve_kernel_seg<256> (deep)" if top == 3 else
+    dt = (tuning or {}).get("deep_threads") or 256
+    kname = (f"solve_kernel_seg<{dt}> (deep)" if top == 3 else
              STAGES[top].replace("solve_kernel<32>", "solve_kernel_seg<32>")
              .replace("root_kernel", "root_kernel_seg"))
     traffic = stage_traffic({1: "pool_kernel multi-instance",
-                             3: "solve_kernel_seg<256> multi-instance"}.get(top, ""), counters, top)
+                             3: f"solve_kernel_seg<{dt}> multi-instance"}.get(top, ""), counters, top)
 
     fn, toi_bad, off = 0, 0, 0
     for b in wl.batches:
