@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="multi-instance: the default launch shapes instead of the autotuner's")
+    ap.add_argument("--ms-list", default="0,1e-4",
+                    help="degenerate-heavy: the minimum separations each step runs")
     ap.add_argument("--tuning", default=None,
                     help="multi-instance: launch shapes as JSON (deep_threads, deep_slots, "
                          "small_blocks_per_sm, small_cap, pool_cap) instead of the autotuner's")
@@ -261,7 +263,8 @@ def make_jobs(args, seed):
     from paper_2009_13349_gb300 import workloads as W
     if args.workload == "degenerate-heavy":
         wl = W.degenerate_heavy(n=args.n, seed=seed)
-        return wl, [(b, ms) for ms in (0.0, 1e-4) for b in wl.batches]
+        ms_list = [float(x) for x in args.ms_list.split(",")]
+        return wl, [(b, ms) for ms in ms_list for b in wl.batches]
     wl = make_workload(args.n, seed)
     return wl, [(b, 0.0) for b in wl.batches]
 
@@ -299,9 +302,10 @@ def workload_config(args):
     if args.workload == "degenerate-heavy":
         return {"workload": f"degenerate-heavy {args.n} queries per GPU (VF:EE 1:1; coplanar, "
                             f"collinear, parallel-edge, vertex-on-vertex and grazing-tangent "
-                            f"motions on a 2^-20 grid), seed {args.seed}, each step at ms = 0 "
-                            f"and at ms = 1e-4",
-                "delta": 1e-6, "max_itr": args.max_itr, "ms": [0.0, 1e-4]}
+                            f"motions on a 2^-20 grid), seed {args.seed}, each step at ms = "
+                            + " and at ms = ".join(args.ms_list.split(",")),
+                "delta": 1e-6, "max_itr": args.max_itr,
+                "ms": [float(x) for x in args.ms_list.split(",")]}
     return {"workload": f"simulation-mixed {args.n} queries per GPU (VF:EE 1:1), seed {args.seed}",
             "delta": 1e-6, "max_itr": args.max_itr, "ms": 0.0}
 

@@ -92,6 +92,7 @@ constexpr int SEG_DEEP_THREADS = 256;
 // and a block that finds none defers its query, so the size changes speed
 // only).  Peak use on the degenerate-heavy workload is about a quarter.
 constexpr int DEEP_POOL_BLOCKS_PER_SM = 3;
+constexpr long long DEEP_MIN_PAGES = 3;   // pages per deep block a launch can count on
 constexpr long long BIGL = 0x7fffffffffffffffLL;
 
 struct Box {
@@ -2568,14 +2569,26 @@ long long pages_for(long long boxes) { return (boxes + PAGE_BOXES - 1) / PAGE_BO
 
 // Pages a default workspace provides: one level of the largest size any
 // level can reach (2 m_I boxes), and at least two, for every deep block up to
-// DEEP_POOL_BLOCKS_PER_SM per SM.
+// DEEP_POOL_BLOCKS_PER_SM per SM; and at least DEEP_MIN_PAGES per deep block.
 long long default_pages(long long nb_deep, long long max_itr)
 {
     const int sms = device_sms();
     const long long cap_blocks = (long long)DEEP_POOL_BLOCKS_PER_SM * (sms > 0 ? sms : 1);
-    if (nb_deep > cap_blocks) nb_deep = cap_blocks;
-    long long per = pages_for(deep_cap(max_itr));
-    return nb_deep * (per < 2 ? 2 : per);
+    const long long per = pages_for(deep_cap(max_itr));
+    const long long full = (nb_deep < cap_blocks ? nb_deep : cap_blocks) * (per < 2 ? 2 : per);
+    return full > DEEP_MIN_PAGES * nb_deep ? full : DEEP_MIN_PAGES * nb_deep;
+}
+
+// Deep blocks a launch runs on a pool of npages shared by `sharers` deep
+// launches at once: every block holds a page for its current level and
+// reserves pages for the next, so a block per DEEP_MIN_PAGES pages at most
+// (a block that finds the pool empty defers its query to the full-size
+// slots, which take deferred queries two at a time).
+int page_limited_blocks(int nb, long long npages, int sharers)
+{
+    const long long lim = npages / (DEEP_MIN_PAGES * (long long)(sharers > 0 ? sharers : 1));
+    if (lim < (long long)nb) nb = (int)(lim > 1 ? lim : 1);
+    return nb;
 }
 
 size_t pool_bytes(long long npages)
@@ -2730,6 +2743,7 @@ ccd_status run_batch(const double *verts, int64_t n, const double *err, int err_
             per_sm = 1;
         if (per_sm > DEEP_BLOCKS_PER_SM) per_sm = DEEP_BLOCKS_PER_SM;
         if (nb_deep > per_sm * sms) nb_deep = per_sm * sms;
+        if (D.paged) nb_deep = page_limited_blocks(nb_deep, D.npages, 1);
     }
     solve_kernel<KIND, SMALL_THREADS><<<L.nb_small, SMALL_THREADS, tq_small, st>>>(
         p, 0, (Box *)(ws + L.off_small), L.cap_small, PagePool{}, p.mid, &h->mid, &h->head_small,
@@ -3031,6 +3045,7 @@ ccd_status multi_plan(const double *verts, int64_t n, const ccd_segment *segs, i
                m.D.cap_deep < deep_cap(max_itr_bound)) {
         return CCD_ERR_WORKSPACE;
     }
+    if (m.D.paged && !shared) m.D.nb_deep = page_limited_blocks(m.D.nb_deep, m.D.npages, 1);
     char *ws = (char *)workspace;
     Params &p = m.p;
     p.verts = verts; p.n = n; p.err = nullptr; p.err_stride = 0;
@@ -3203,11 +3218,20 @@ PagePool to_pages(const FrontierPool &f)
     return p;
 }
 
+// A served batch's deep launches use the server's block size (see
+// served_deep_threads) and share its pool with every other lane's: each
+// takes its share of the pool's pages in blocks.
 ccd_status plan(const ServedBatch &b, const FrontierPool &pool, MultiPlan *M)
 {
     const PagePool pages = to_pages(pool);
+    const int sms = device_sms();
+    if (sms <= 0) return CCD_ERR_CUDA;
+    const int dt = pool.deep_threads ? pool.deep_threads : SEG_DEEP_THREADS;
+    const ccd_tuning t = {dt, page_limited_blocks(deep_blocks_per_sm(dt) * sms, pool.npages,
+                                                  pool.sharers),
+                          0, 0, 0};
     return multi_plan(b.verts, b.n, b.segs, b.nseg, b.max_itr_bound, b.collides, b.toi,
-                      b.out_tol, b.checks, nullptr, b.workspace, b.ws_bytes, &pages, M);
+                      b.out_tol, b.checks, &t, b.workspace, b.ws_bytes, &pages, M);
 }
 }  // namespace
 
@@ -3229,12 +3253,25 @@ size_t served_workspace_bytes(int64_t n, int64_t max_itr_bound)
     if (n < 0 || n >= 0x7fffffffLL || max_itr_bound <= 0) return 0;
     const int sms = device_sms();
     Tuned T;
-    if (sms <= 0 || !resolve_tuning(nullptr, sms, &T)) return 0;
+    if (sms <= 0 || !resolve_tuning(nullptr, sms, &T)) return 0;   // deep shapes: no bytes
     return multi_fixed_bytes(n, sms, T) +
            JUMBO_SLOTS * align256(sizeof(Box) * 2 * (size_t)deep_cap(max_itr_bound));
 }
 
 size_t header_bytes() { return sizeof(Header); }
+
+// The server's deep block size: 128 threads (six blocks per SM, the faster
+// form for batches of expensive requests with many deep queries) when its
+// pool leaves DEEP_MIN_PAGES pages to every such block of every lane and
+// kind at once; 256 (three per SM) otherwise, so that a small arena's
+// blocks still find pages.
+int served_deep_threads(long long npages, int lanes)
+{
+    const int sms = device_sms();
+    const long long need =
+        DEEP_MIN_PAGES * 2LL * (lanes > 0 ? lanes : 1) * deep_blocks_per_sm(DEEP_THREADS) * (sms > 0 ? sms : 1);
+    return npages >= need ? DEEP_THREADS : SEG_DEEP_THREADS;
+}
 
 ccd_status served_front(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st)
 {

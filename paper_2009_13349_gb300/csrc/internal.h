@@ -19,6 +19,8 @@ struct FrontierPool {
     int nwords;                  // (npages + 63) / 64
     long long npages;
     int *counters;               // 2 ints: pages held now, the most held at once
+    int deep_threads;            // deep-solver block size of the batches on the pool
+    int sharers;                 // deep launches that may use the pool at once
 };
 
 size_t page_bytes();
@@ -46,6 +48,8 @@ struct ServedBatch {
 
 size_t served_workspace_bytes(int64_t n, int64_t max_itr_bound);
 size_t header_bytes();
+// deep-solver block size for a server with npages pool pages and `lanes` lanes
+int served_deep_threads(long long npages, int lanes);
 // header reset, validation, level 0, pooled and one-warp stages, deep list
 ccd_status served_front(const ServedBatch &b, const FrontierPool &pool, cudaStream_t st);
 // one deep round: until the deep list is empty, slice_ns has passed (> 0)

@@ -418,6 +418,8 @@ ccd_status ccd_batch_begin(const ccd_server_config *config, ccd_server **out)
     S->pool.pages = a + al256(sizeof(unsigned long long) * (size_t)S->pool.nwords);
     S->pool.npages = np;
     S->pool.counters = counters;
+    S->pool.sharers = 2 * c.lanes;   // each lane's two deep launches (VF, EE)
+    S->pool.deep_threads = served_deep_threads(np, c.lanes);
     if (cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking) != cudaSuccess ||
         cudaHostAlloc((void **)&S->h_ring, sizeof(ccd_segment) * (size_t)c.max_requests,
                       cudaHostAllocDefault) != cudaSuccess) {
