@@ -204,10 +204,13 @@ ccd_status ccd_workspace_counters(const void *workspace, int64_t *counters, int3
  * batch call records events[0] before the level-0 kernel, events[1] after
  * it, events[2] after the pooled solver, events[3] after the one-warp
  * solver and events[4] after the deep solver, on the call's stream
- * (ccd_multi_batch has no pooled stage and records events[1] and [2]
- * back to back).  The events (cudaEvent_t, created by
- * the caller) are not retained beyond the next ccd_set_stage_events call;
- * count == 0 switches recording off.  Process-wide; not thread-safe.
+ * (ccd_multi_batch records events[0] after its segment validation).  The
+ * events (cudaEvent_t, created by the caller) are not retained beyond the
+ * next ccd_set_stage_events call; count == 0 switches recording off.  A call
+ * captured into a CUDA graph while they are set records them at every
+ * replay of that graph, so they must outlive the graph: replaying it after
+ * destroying them is undefined (a crash on GB300).  Process-wide; not
+ * thread-safe.
  */
 ccd_status ccd_set_stage_events(void *const *events, int count);
 
