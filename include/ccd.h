@@ -273,6 +273,12 @@ size_t ccd_multi_workspace_bytes(int64_t n, int64_t max_itr_bound, const ccd_tun
  * max_itr_bound, t_max outside (0, 1] or group < 0, sets the workspace
  * status to CCD_ERR_ARG and no query is answered.  Host-side errors as for ccd_vf_batch, plus CCD_ERR_ARG for
  * nseg < 1 with n > 0, a NULL segs, or an invalid tuning.
+ * The two kinds' deep launches run at once: the second on a
+ * stream of the library's own (one per calling stream, created on the first
+ * call from that stream made outside a CUDA graph capture), forked from and
+ * joined back into `stream` with events, so the call stays ordered on
+ * `stream`.  A first call captured before any uncaptured call from its
+ * stream runs the two kinds one after the other.
  */
 ccd_status ccd_multi_batch(const double *verts, int64_t n, const ccd_segment *segs, int32_t nseg,
                            int64_t max_itr_bound, uint8_t *collides, double *toi,

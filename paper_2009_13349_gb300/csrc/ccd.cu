@@ -53,6 +53,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace {
 
 constexpr int KMAX = 53;              // deepest dyadic level per dimension
@@ -3003,6 +3005,61 @@ size_t multi_fixed_bytes(long long n, int sms, const Tuned &T)
 // One segmented batch, laid out in its workspace.  The deep tier's pages are
 // the workspace's own, or (served batches) a pool shared with other batches,
 // in which case the workspace holds only the full-size slots.
+// A second stream per caller stream, for the second kind's launch of a
+// segmented batch's deep stage: the two kinds' launches are independent, and
+// run at once each fills the other's tail (the 20M-query step's deep stage
+// took 24 ms against 33).  Fork and join
+// go through events, so they also hold inside a CUDA graph capture.  The
+// stream and events are created on a call made outside capture (creating
+// them during capture is not attempted); without them the launches run one
+// after the other on the caller's stream.  A process keeps at most 32.
+struct SideStream {
+    cudaStream_t caller, side;
+    cudaEvent_t fork, join;
+};
+std::mutex g_side_mu;
+SideStream g_side[32];
+int g_nside = 0;
+
+const SideStream *side_for(cudaStream_t caller)
+{
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    for (int i = 0; i < g_nside; ++i)
+        if (g_side[i].caller == caller) return &g_side[i];
+    if (g_nside == 32) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return nullptr;
+    SideStream x{caller, nullptr, nullptr, nullptr};
+    if (cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+        if (x.fork) cudaEventDestroy(x.fork);
+        cudaStreamDestroy(x.side);
+        return nullptr;
+    }
+    g_side[g_nside] = x;
+    return &g_side[g_nside++];
+}
+
+// Starts the second kind's launch: returns the stream to launch it on (the
+// side stream after a fork from `st`, or `st` itself).
+cudaStream_t fork_side(const SideStream *sd, cudaStream_t st)
+{
+    if (!sd || cudaEventRecord(sd->fork, st) != cudaSuccess ||
+        cudaStreamWaitEvent(sd->side, sd->fork, 0) != cudaSuccess)
+        return st;
+    return sd->side;
+}
+
+// Joins the side stream back into `st` (after fork_side returned it).
+bool join_side(const SideStream *sd, cudaStream_t st, cudaStream_t used)
+{
+    if (used == st) return true;
+    return cudaEventRecord(sd->join, used) == cudaSuccess &&
+           cudaStreamWaitEvent(st, sd->join, 0) == cudaSuccess;
+}
+
 struct MultiPlan {
     Params p;
     Tuned T;
@@ -3045,7 +3102,8 @@ ccd_status multi_plan(const double *verts, int64_t n, const ccd_segment *segs, i
                m.D.cap_deep < deep_cap(max_itr_bound)) {
         return CCD_ERR_WORKSPACE;
     }
-    if (m.D.paged && !shared) m.D.nb_deep = page_limited_blocks(m.D.nb_deep, m.D.npages, 1);
+    // the two kinds' deep launches share the pool at once
+    if (m.D.paged && !shared) m.D.nb_deep = page_limited_blocks(m.D.nb_deep, m.D.npages, 2);
     char *ws = (char *)workspace;
     Params &p = m.p;
     p.verts = verts; p.n = n; p.err = nullptr; p.err_stride = 0;
@@ -3114,7 +3172,9 @@ ccd_status multi_front(const MultiPlan &M, bool init_pool, cudaStream_t st)
         p, M.segs, M.nseg);
     stage_mark(1, st);
     const size_t tq_small = sizeof(double) * 2 * SMALL_THREADS * TWidth<CCD_KIND_EE>::W;
-    // pooled stage: one launch per kind over the survivor list
+    // pooled stage: one launch per kind over the survivor list, one after the
+    // other (run at once they slowed each other: 817 against 790 ms for the
+    // 20M-query step's pooled stage)
     pool_kernel<CCD_KIND_VF><<<pool_blocks(pool_kernel<CCD_KIND_VF>, M.sms), 32, 0, st>>>(
         p, M.pool_mem, M.pool_meta, M.T.pool_cap, p.surv, &p.hdr->survivors, &p.hdr->head_pool,
         M.segs, M.nseg);
@@ -3140,11 +3200,16 @@ void multi_deep_launch(const MultiPlan &M, long long slice_ns, const volatile in
     const size_t tq_deep = sizeof(SharedUV<DT>);
     Box *slots = (Box *)(M.ws + M.D.off_slots);
     if (M.D.paged) {
+        // the two kinds at once on the shared page pool
+        const SideStream *sd = side_for(st);
+        const cudaStream_t st2 = fork_side(sd, st);
+        solve_kernel_seg<DT, true, CCD_KIND_EE><<<M.D.nb_deep, DT, tq_deep, st2>>>(
+            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
         solve_kernel_seg<DT, true, CCD_KIND_VF><<<M.D.nb_deep, DT, tq_deep, st>>>(
             M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
-        solve_kernel_seg<DT, true, CCD_KIND_EE><<<M.D.nb_deep, DT, tq_deep, st>>>(
-            M.p, M.segs, M.nseg, 1, nullptr, 0, M.pages, slice_ns, yield);
+        join_side(sd, st, st2);
     } else {
+        // contiguous slots are one set for both kinds: one after the other
         solve_kernel_seg<DT, false, CCD_KIND_VF><<<M.D.nb_deep, DT, tq_deep, st>>>(
             M.p, M.segs, M.nseg, 1, slots, M.D.cap_deep, PagePool{});
         solve_kernel_seg<DT, false, CCD_KIND_EE><<<M.D.nb_deep, DT, tq_deep, st>>>(
@@ -3544,8 +3609,6 @@ ccd_status ccd_segments_err_from_bounds(const double *verts, int64_t n, ccd_segm
 // check limit of at most STATIC_MAX_ITR per call; the one-warp stage has
 // slots for STATIC_SMALL_BLOCKS blocks and launches four per SM, at most
 // that many.
-
-#include <mutex>
 
 namespace {
 
